@@ -1,0 +1,448 @@
+#!/usr/bin/env python
+"""Benchmark of the Hive hash table on GB300: Gops/s for bulk insert, find and
+mixed batches at 95% load on one fixed 2^26-slot table.
+
+One step = clear the table, bulk-insert 63,753,421 unique uniform keys (95% of
+2^26 slots), run 2^26 finds at a 50% hit rate, then a mixed batch of 2^24 ops
+(insert:find:erase = 1:2:1, new keys / live keys / live keys) that holds the load
+at 95%.  Value = all ops of the step / step time.  Inputs and the 512 MiB table
+are larger than L2, so nothing is flushed between steps.
+
+Multi-GPU: one process per GPU, each holding its own shard (an independent
+table with its own seeded keys); no data-path collective ("scaling": "weak").
+
+``--impl reference`` runs the CPU oracle (a plain single-threaded dictionary)
+on a bounded sample of the same workload, as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Gops/s insert/find/mixed at 95% load"
+SLOTS = 1 << 26
+LOAD = (19, 20)
+N_FIND = 1 << 26
+N_MIXED = 1 << 24
+SEED = 2
+KERNEL_SRC = os.path.join(ROOT, "paper_2510_15095_gb300", "csrc", "hive_kernels.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["own", "reference"], default="own")
+    ap.add_argument("--slots", type=int, default=SLOTS)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 22,
+                    help="inserts (and as many finds) in the CPU oracle sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_workload(seed: int, slots: int):
+    from paper_2510_15095_gb300 import workload as W
+    w = W.fill_and_query(seed=seed, slots=slots, load_num=LOAD[0], load_den=LOAD[1],
+                         n_find=N_FIND if slots == SLOTS else slots)
+    n_mixed = N_MIXED if slots == SLOTS else max(slots // 4, 64)
+    rng = np.random.default_rng(seed + 77)
+    n_ins = n_mixed // 4
+    n_er = n_mixed // 4
+    n_fd = n_mixed - n_ins - n_er
+    # new keys: counters beyond the insert keys and the absent query keys
+    new, _ = W.take_keys(seed, 1 << 31, n_ins)
+    ops, keys, vals = W.mixed_batch(rng, w["insert_keys"], new, n_ins, n_er, n_fd, seed=seed)
+    w.update({"mix_ops": ops, "mix_keys": keys, "mix_vals": vals})
+    return w
+
+
+def workload_config(w, slots):
+    n_ins = int(w["insert_keys"].size)
+    return {
+        "workload": (f"fixed table of {slots} slots (S=32 buckets); bulk insert {n_ins} unique "
+                     f"uniform u32 keys (95% load), {w['find_keys'].size} finds at 50% hit "
+                     f"(uniform), mixed batch of {w['mix_ops'].size} ops insert:find:erase 1:2:1 "
+                     "at 95% load"),
+        "slots": slots, "load": LOAD[0] / LOAD[1], "n_insert": n_ins,
+        "n_find": int(w["find_keys"].size), "n_mixed": int(w["mix_ops"].size),
+        "key_dist": "uniform u32 in [1, 2^32-3], unique per batch", "seed": SEED,
+        "l2": "no flush: 512 MiB table and inputs exceed the 129 MB L2",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.path = tempfile.mktemp(prefix="clk_", suffix=".csv")
+        self.f = open(self.path, "w")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def gpu_select(torch, dev) -> str:
+    """nvidia-smi -i argument for this process's GPU (UUID when available)."""
+    import re
+    u = str(getattr(torch.cuda.get_device_properties(dev), "uuid", ""))
+    m = re.search(r"[0-9a-fA-F]{8}-[0-9a-fA-F]{4}-[0-9a-fA-F]{4}-[0-9a-fA-F]{4}-[0-9a-fA-F]{12}", u)
+    if m:
+        return "GPU-" + m.group(0)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis:
+        return vis.split(",")[dev.index].strip()
+    return str(dev.index)
+
+
+# ---------------------------------------------------------------------------
+# roofline helpers
+# ---------------------------------------------------------------------------
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    try:
+        sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        for line in open(TRAFFIC_FILE):
+            if line.startswith("#") or "=" not in line:
+                continue
+            kv = dict(tok.split("=", 1) for tok in line.split())
+            if kv.get("kernel") == kernel and kv.get("source_sha") == sha:
+                return float(kv["bytes_per_launch"]), kv
+    except Exception:
+        pass
+    return None, None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(w, n_sample: int):
+    """Time the oracle on a prefix sample: n inserts, n finds, n/4 mixed ops."""
+    import oracle
+    d = oracle.Dict()
+    ins_k = w["insert_keys"][:n_sample]
+    ins_v = w["insert_vals"][:n_sample]
+    fk = w["find_keys"][:n_sample]
+    nm = min(n_sample // 4, w["mix_ops"].size)
+    t0 = time.perf_counter()
+    d.insert(ins_k, ins_v)
+    d.find(fk)
+    d.execute(w["mix_ops"][:nm], w["mix_keys"][:nm], w["mix_vals"][:nm])
+    dt = time.perf_counter() - t0
+    ops = ins_k.size + fk.size + nm
+    return ops, dt
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    w = make_workload(SEED, args.slots)
+    # bound the whole run: about 2^25 oracle ops over all steps
+    per_step = max(1 << 16, (1 << 25) // max(args.steps + args.warmup, 1) * 4 // 9)
+    n = min(args.cpu_sample, per_step, w["insert_keys"].size)
+    for _ in range(args.warmup):
+        oracle_sample(w, n // 8)
+    times, ops = [], 0
+    for _ in range(args.steps):
+        ops, dt = oracle_sample(w, n)
+        times.append(dt)
+    v = ops * len(times) / sum(times) / 1e9
+    sample = (f"prefix sample per step: {n} inserts, {n} finds, {n // 4} mixed ops "
+              f"of the {args.slots}-slot workload")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gops/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": workload_config(w, args.slots),
+            "cpu_baseline": {"value": v, "unit": "Gops/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "Gops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# own arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2510_15095_gb300 import hive as H
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    seed = SEED + rank  # each rank owns an independent shard
+    w = make_workload(seed, args.slots)
+    cfg = workload_config(w, args.slots)
+    up = lambda a: H.to_device_u32(a, dev)  # noqa: E731
+    ik, iv, fk = up(w["insert_keys"]), up(w["insert_vals"]), up(w["find_keys"])
+    mo = torch.from_numpy(w["mix_ops"]).to(dev)
+    mk, mv = up(w["mix_keys"]), up(w["mix_vals"])
+    n_ins, n_find, n_mix = ik.numel(), fk.numel(), mk.numel()
+    ins_st = torch.empty(n_ins, dtype=torch.uint8, device=dev)
+    f_val = torch.empty(n_find, dtype=torch.int32, device=dev)
+    f_fnd = torch.empty(n_find, dtype=torch.uint8, device=dev)
+    t = H.HiveTable(args.slots)
+    stream = torch.cuda.current_stream(dev)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def step(times=None):
+        t.clear()
+        if times is not None:
+            ev[0].record(stream)
+        t.insert(ik, iv, status=ins_st)
+        if times is not None:
+            ev[1].record(stream)
+        t.find(fk, vals_out=f_val, found=f_fnd)
+        if times is not None:
+            ev[2].record(stream)
+        mvo, mst = t.execute(mo, mk, mv)
+        if times is not None:
+            ev[3].record(stream)
+            torch.cuda.synchronize(dev)
+            times.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]),
+                          ev[2].elapsed_time(ev[3])))
+        return mvo, mst
+
+    # warm-up, then a correctness gate on the last warm-up step
+    for _ in range(max(args.warmup, 1)):
+        mvo, mst = step()
+    torch.cuda.synchronize(dev)
+    assert bool((ins_st == H.INSERTED).all()), "bulk insert did not insert every key"
+    hits = torch.from_numpy(w["is_hit"]).to(dev)
+    assert bool(((f_fnd == 1) == hits).all()), "find flags disagree with the workload"
+    assert t.check() == 0
+
+    # per-phase breakdown and bucket probes (outside the timed region)
+    phase_ms = []
+    for _ in range(3):
+        step(phase_ms)
+    t.clear()
+    t.insert(ik, iv, status=ins_st)
+    s_ins = t.stats()
+    t.find(fk, vals_out=f_val, found=f_fnd)
+    s_find = t.stats()
+    probes_ins = s_ins["probes"]
+    probes_find = s_find["probes"] - s_ins["probes"]
+    overflowed = s_ins["overflowed"]
+    stashed = s_ins["stashed"]
+
+    # timed region
+    gpu_id = gpu_select(torch, dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.2)
+    t.profile(True)
+    t.profile_read()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    prof = t.profile_read()
+    t.profile(False)
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        x = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        ms = float(x.item())
+    ops_step = n_ins + n_find + n_mix
+    value = ops_step * args.steps * world / (ms / 1e3) / 1e9
+    gpu_launches = sum(c for _, c in prof.values())
+
+    # roofline of the dominant kernel (algorithmic bytes per op x ops per launch)
+    peak, peak_kind = measured_peak()
+    ins_ms = prof.get("insert", (0.0, 1))
+    find_ms = prof.get("find", (0.0, 1))
+    bytes_find = 9 * n_find + 256 * probes_find  # key in, value + flag out, probed buckets
+    bytes_ins = 9 * n_ins + 256 * probes_ins + 32 * (n_ins - overflowed)  # + one written sector
+    rl = {}
+    for name, (tot, cnt), byts, kname in (("insert", ins_ms, bytes_ins, "k_ops<insert>"),
+                                            ("find", find_ms, bytes_find, "k_ops<find>")):
+        avg = tot / max(cnt, 1)
+        ach = byts / (avg / 1e3) / 1e9 if avg > 0 else 0.0
+        traffic, _ = recorded_traffic(kname)
+        rl[name] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": traffic, "algorithmic_bytes": byts,
+                    "avg_ms": avg, "kernel": kname, "peak_source": peak_kind}
+    dom = "insert" if ins_ms[0] >= find_ms[0] else "find"
+    roofline = dict(rl[dom])
+    roofline["others"] = {k: v for k, v in rl.items() if k != dom}
+
+    ph = np.array(phase_ms)
+    phases = {"insert_gops": n_ins / (ph[:, 0].mean() / 1e3) / 1e9,
+              "find_gops": n_find / (ph[:, 1].mean() / 1e3) / 1e9,
+              "mixed_gops": n_mix / (ph[:, 2].mean() / 1e3) / 1e9,
+              "insert_ms": float(ph[:, 0].mean()), "find_ms": float(ph[:, 1].mean()),
+              "mixed_ms": float(ph[:, 2].mean()),
+              "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+              "probes_per_find": probes_find / n_find, "probes_per_insert": probes_ins / n_ins,
+              "insert_overflowed": overflowed, "insert_stashed": stashed}
+
+    # end to end through the public API with pinned host buffers
+    h_ik = torch.from_numpy(w["insert_keys"].view(np.int32)).pin_memory()
+    h_iv = torch.from_numpy(w["insert_vals"].view(np.int32)).pin_memory()
+    h_fk = torch.from_numpy(w["find_keys"].view(np.int32)).pin_memory()
+    h_mo = torch.from_numpy(w["mix_ops"]).pin_memory()
+    h_mk = torch.from_numpy(w["mix_keys"].view(np.int32)).pin_memory()
+    h_mv = torch.from_numpy(w["mix_vals"].view(np.int32)).pin_memory()
+    o_st = torch.empty(n_ins, dtype=torch.uint8).pin_memory()
+    o_fv = torch.empty(n_find, dtype=torch.int32).pin_memory()
+    o_ff = torch.empty(n_find, dtype=torch.uint8).pin_memory()
+    o_mv = torch.empty(n_mix, dtype=torch.int32).pin_memory()
+    o_ms = torch.empty(n_mix, dtype=torch.uint8).pin_memory()
+    d_ik, d_iv, d_fk = torch.empty_like(ik), torch.empty_like(iv), torch.empty_like(fk)
+    d_mo, d_mk, d_mv = torch.empty_like(mo), torch.empty_like(mk), torch.empty_like(mv)
+
+    def e2e_step():
+        t.clear()
+        d_ik.copy_(h_ik, non_blocking=True)
+        d_iv.copy_(h_iv, non_blocking=True)
+        t.insert(d_ik, d_iv, status=ins_st)
+        o_st.copy_(ins_st, non_blocking=True)
+        d_fk.copy_(h_fk, non_blocking=True)
+        t.find(d_fk, vals_out=f_val, found=f_fnd)
+        o_fv.copy_(f_val, non_blocking=True)
+        o_ff.copy_(f_fnd, non_blocking=True)
+        d_mo.copy_(h_mo, non_blocking=True)
+        d_mk.copy_(h_mk, non_blocking=True)
+        d_mv.copy_(h_mv, non_blocking=True)
+        vo, st = t.execute(d_mo, d_mk, d_mv)
+        o_mv.copy_(vo, non_blocking=True)
+        o_ms.copy_(st, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        x = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        e2e_ms = float(x.item())
+    h2d = 4 * (2 * n_ins + n_find + 2 * n_mix) + n_mix
+    d2h = n_ins + 5 * n_find + 5 * n_mix
+    e2e = {"value": ops_step * args.e2e_steps * world / (e2e_ms / 1e3) / 1e9, "unit": "Gops/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
+    assert bool((o_ff.numpy() == w["is_hit"]).all()), "e2e find flags disagree"
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n = min(args.cpu_sample, n_ins)
+        ops, dt = oracle_sample(w, n)
+        cpu = {"value": ops / dt / 1e9, "unit": "Gops/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} inserts + {n} finds + {n // 4} mixed ops (prefix of the workload), "
+                         f"{dt:.1f} s single-threaded std::unordered_map"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gops/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u32/u64", "data": "synthetic", "config": cfg, "phases": phases,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": gpu_launches}
+        print(json.dumps(line), flush=True)
+    t.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

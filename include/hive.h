@@ -1,0 +1,233 @@
+/*
+ * hive.h -- C ABI of the Hive hash table on one GB300 GPU (sm_103a).
+ *
+ * The table is the one of "Hive Hash Table: A Warp-Cooperative, Dynamically
+ * Resizable Hash Table for GPUs" (arXiv 2510.15095): 32-bit keys and 32-bit
+ * values packed into 64-bit words (Section III-A), buckets of S slots with a
+ * per-bucket free mask and lock plus an overflow stash (Section III-B), two
+ * candidate buckets per key from BitHash1/BitHash2 (Section III-C), insert by
+ * replace -> claim-then-commit -> bounded cuckoo eviction -> stash
+ * (Section IV-A, Algorithms 1-3), lookup and delete by warp match-and-elect
+ * (Section IV-B, Algorithm 4), and linear-hashing growth and shrinkage in
+ * batches of K bucket pairs (Section IV-C).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Op arrays (keys, values, op codes, outputs) are DEVICE pointers owned by
+ *    the caller (any memory the GPU can address).  They must stay valid until
+ *    the work queued on `stream` has completed.  `stream` is a cudaStream_t
+ *    passed as void*; NULL means the legacy default stream.
+ *  - Calls are stream-ordered and asynchronous unless stated otherwise.  A
+ *    fixed-capacity table never synchronises inside insert/find/erase/execute.
+ *    A resizable table reads a few counters back to the host after each
+ *    mutating call (to apply the load-factor policy), so those calls return
+ *    after the work on `stream` has completed.
+ *  - n == 0 is a no-op that returns HIVE_OK.  A NULL table, a NULL required
+ *    array with n > 0, or n >= 2^32 returns HIVE_ERR_INVALID_ARG and queues
+ *    nothing.
+ *  - Keys 0xFFFFFFFE and 0xFFFFFFFF are reserved (0xFFFFFFFF'FFFFFFFF is the
+ *    empty-slot word).  An op on a reserved key is skipped, reports
+ *    HIVE_ST_RESERVED_KEY, and raises the table's sticky error word, which
+ *    hive_check() returns.  Values are unrestricted.
+ *  - Batch contract: within one call no key may appear in more than one update
+ *    (insert or erase), and in hive_execute no key may be both updated and
+ *    searched.  Repeated finds of one key are allowed.  Under this contract
+ *    every result is unique and equals applying the ops one by one to a
+ *    dictionary.  Outside it the outcome is some serialisation of the batch.
+ *  - A table is driven by one host thread at a time.  No C++ exception
+ *    crosses this interface.  hive_last_error() describes the last failure of
+ *    the calling thread.
+ */
+#ifndef HIVE_H_
+#define HIVE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hive_table hive_table; /* opaque; the library owns all table memory */
+
+typedef enum {
+  HIVE_OK = 0,
+  HIVE_ERR_INVALID_ARG = 1,  /* bad pointer, size or configuration */
+  HIVE_ERR_RESERVED_KEY = 2, /* sticky: an op used a reserved key */
+  HIVE_ERR_OOM = 3,          /* device allocation failed; table unchanged */
+  HIVE_ERR_FULL = 4,         /* sticky: fixed table had no room for some insert */
+  HIVE_ERR_TIMEOUT = 5,      /* sticky: a bounded wait gave up (bucket lock) */
+  HIVE_ERR_CUDA = 6,         /* a CUDA runtime call failed */
+  HIVE_ERR_CONTRACT = 7      /* sticky: batch contract violated (concurrent update of one key) */
+} hive_status;
+
+/* Per-op result codes (one byte per op). */
+enum {
+  HIVE_ST_INSERTED = 0,     /* insert of an absent key */
+  HIVE_ST_REPLACED = 1,     /* insert of a present key: value overwritten */
+  HIVE_ST_ERASED = 2,       /* erase of a present key */
+  HIVE_ST_NOT_FOUND = 3,    /* erase or find of an absent key */
+  HIVE_ST_FOUND = 4,        /* find of a present key (hive_execute only) */
+  HIVE_ST_FULL = 5,         /* insert dropped: fixed table and stash full */
+  HIVE_ST_RESERVED_KEY = 6  /* op on a reserved key, skipped */
+};
+
+/* Op codes for hive_execute (one byte per op). */
+enum { HIVE_OP_INSERT = 0, HIVE_OP_FIND = 1, HIVE_OP_ERASE = 2 };
+
+/* Placement of a new key among its two candidate buckets (Section V: "bucketed
+ * two-choice placement").  BALANCED picks the bucket with more free slots
+ * (ties go to the BitHash1 bucket); FIRST picks the BitHash1 bucket whenever it
+ * has room. */
+enum { HIVE_PLACE_BALANCED = 0, HIVE_PLACE_FIRST = 1 };
+
+typedef struct {
+  uint64_t initial_slots;   /* capacity at creation; rounded up to whole buckets */
+  uint64_t max_slots;       /* resizable: growth limit (memory reserved up front);
+                               ignored for fixed tables */
+  uint32_t bucket_slots;    /* S, slots per bucket: 32 (Section III-A) */
+  uint32_t max_evictions;   /* cuckoo displacement bound (Section III-B), >= 1 */
+  uint32_t resize_batch;    /* K, bucket pairs per split/merge launch (Section IV-C) */
+  uint32_t stash_permille;  /* stash capacity as a fraction of slots, in 1/1000
+                               (Section IV-A step 4: "typically 1-2%") */
+  uint32_t grow_num, grow_den;     /* expand while load > grow_num/grow_den (0.9) */
+  uint32_t shrink_num, shrink_den; /* contract while load < shrink_num/shrink_den */
+  uint32_t resizable;       /* 0: fixed capacity; 1: linear-hashing resize */
+  uint32_t placement;       /* HIVE_PLACE_* */
+  uint32_t lock_spin_limit; /* tries before a bucket-lock wait gives up */
+  uint32_t reserved0;       /* must be 0 */
+} hive_config;
+
+/* Per-table counters, accumulated since creation or the last hive_clear.
+ * Steps follow Section IV-A: step 1 replace, step 2 claim-then-commit,
+ * step 3 bounded cuckoo eviction, step 4 overflow stash. */
+typedef struct {
+  uint64_t replaced;         /* inserts finished in step 1 */
+  uint64_t claimed_fast;     /* inserts finished in step 2 by the bulk kernel */
+  uint64_t overflowed;       /* inserts handed to the eviction kernel */
+  uint64_t claimed_slow;     /* of those, placed by a lock-free claim */
+  uint64_t evict_rounds;     /* displacement rounds executed (step 3) */
+  uint64_t lock_acquired;    /* bucket locks taken */
+  uint64_t lock_timeouts;    /* bounded lock waits that gave up */
+  uint64_t stashed;          /* words appended to the stash (step 4) */
+  uint64_t pending;          /* inserts that found no room (FULL or re-run after growth) */
+  uint64_t stash_reinserted; /* stash words moved back into buckets by maintenance */
+  uint64_t splits;           /* bucket pairs split */
+  uint64_t merges;           /* bucket pairs merged */
+  uint64_t probes;           /* 256-byte bucket reads by the bulk kernel (Section IV-B:
+                                one per candidate bucket examined) */
+  uint64_t stash_lookups;    /* binary searches of the stash by the bulk kernel */
+} hive_stats_t;
+
+/* Kernel kinds timed by the profiling hook. */
+enum {
+  HIVE_K_FIND = 0,     /* bulk kernel, find batch */
+  HIVE_K_INSERT = 1,   /* bulk kernel, insert batch (steps 1-2) */
+  HIVE_K_ERASE = 2,    /* bulk kernel, erase batch */
+  HIVE_K_MIXED = 3,    /* bulk kernel, mixed batch */
+  HIVE_K_EVICT = 4,    /* eviction + stash kernel (steps 3-4) */
+  HIVE_K_MAINT = 5,    /* stash maintenance */
+  HIVE_K_SPLIT = 6,    /* linear-hashing split */
+  HIVE_K_MERGE = 7,    /* linear-hashing merge and its pre-check */
+  HIVE_K_COUNT = 8,    /* insert counting for a resizable mixed batch */
+  HIVE_K_KINDS = 16
+};
+
+/* Per-kind device time of the kernels launched while profiling was on. */
+typedef struct {
+  double ms[HIVE_K_KINDS];         /* summed kernel time, milliseconds */
+  uint64_t launches[HIVE_K_KINDS]; /* kernels launched */
+} hive_profile_t;
+
+/* Host image of a quiescent table, for tests and checkpoints (hive_dump). */
+typedef struct {
+  uint64_t nb;          /* buckets in use = M + 1 + p */
+  uint32_t S;           /* slots per bucket */
+  uint32_t M;           /* linear-hashing index mask 2^m - 1 */
+  uint32_t p;           /* split pointer */
+  uint32_t reserved0;
+  uint64_t stash_n;     /* stash words in use */
+  uint64_t stash_cap;   /* stash capacity */
+  uint64_t size;        /* live-entry counter */
+  uint64_t pending;     /* words waiting for room (0 at quiescence) */
+  uint64_t* buckets;    /* [nb * S] packed words, or NULL to query sizes only */
+  uint32_t* masks;      /* [nb] free masks, bit i set = slot i free */
+  uint32_t* locks;      /* [nb] lock words */
+  uint64_t* stash;      /* [stash_n] packed words */
+} hive_image;
+
+/* Fills *cfg with defaults: 2^20 slots, S = 32, max_evictions 16, K = 1024,
+ * stash 1%, thresholds 9/10 and 2/5, fixed capacity, balanced placement. */
+void hive_config_default(hive_config* cfg);
+
+/* Creates a table (Section III-B: buckets, freeMask, lock, metadata, stash).
+ * All device memory is allocated here, on the current CUDA device; a resizable
+ * table reserves max_slots up front.  The table is empty on return, and its
+ * initialisation is ordered on `stream`.  Errors: INVALID_ARG (bad config),
+ * OOM (nothing leaked), CUDA. */
+hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out);
+
+/* Frees every allocation of the table.  Synchronises the device first. */
+hive_status hive_destroy(hive_table* t);
+
+/* Insert/Replace (Section III-D; Section IV-A, Algorithms 1-3 and step 4).
+ * keys[n], vals[n]: inputs.  status[n] (nullable): per-op
+ * INSERTED / REPLACED / FULL / RESERVED_KEY. */
+hive_status hive_insert(hive_table* t, const uint32_t* keys, const uint32_t* vals,
+                        uint64_t n, uint8_t* status, void* stream);
+
+/* Search (Section III-D; Section IV-B, WCME).  vals_out[n]: the value, or 0 when
+ * absent.  found[n] (nullable): 1 when present, else 0.  Never mutates. */
+hive_status hive_find(hive_table* t, const uint32_t* keys, uint64_t n, uint32_t* vals_out,
+                      uint8_t* found, void* stream);
+
+/* Delete (Section III-D; Section IV-B, Algorithm 4).  status[n] (nullable):
+ * ERASED / NOT_FOUND / RESERVED_KEY. */
+hive_status hive_erase(hive_table* t, const uint32_t* keys, uint64_t n, uint8_t* status,
+                       void* stream);
+
+/* Mixed batch (Section V-C2, imbalanced workloads).  ops[n] holds HIVE_OP_*.
+ * vals (nullable unless the batch holds inserts) supplies insert values.
+ * vals_out[n] (nullable): find results, 0 otherwise.  status[n] (nullable):
+ * per-op code (finds report FOUND / NOT_FOUND). */
+hive_status hive_execute(hive_table* t, const uint8_t* ops, const uint32_t* keys,
+                         const uint32_t* vals, uint64_t n, uint32_t* vals_out,
+                         uint8_t* status, void* stream);
+
+/* Live entries (buckets + stash).  Synchronises `stream`. */
+hive_status hive_size(hive_table* t, uint64_t* out, void* stream);
+
+/* Current slot capacity S * nBuckets (host-side state, no synchronisation). */
+hive_status hive_capacity(hive_table* t, uint64_t* slots_out);
+
+/* Empties the table and returns it to its initial capacity (stream-ordered). */
+hive_status hive_clear(hive_table* t, void* stream);
+
+/* Reads the sticky device error word, clears it, and returns the first
+ * condition seen (RESERVED_KEY, FULL, TIMEOUT, CONTRACT) or HIVE_OK.
+ * Synchronises `stream`. */
+hive_status hive_check(hive_table* t, void* stream);
+
+/* Copies the counters to *out.  Synchronises `stream`. */
+hive_status hive_stats(hive_table* t, hive_stats_t* out, void* stream);
+
+/* Copies the table into caller-owned host arrays.  With img->buckets == NULL
+ * only the scalar fields are filled (to size the arrays).  Synchronises. */
+hive_status hive_dump(hive_table* t, hive_image* img, void* stream);
+
+/* Turns per-kernel timing on (enable != 0) or off.  While on, every kernel
+ * the table launches is bracketed by two CUDA events recorded on the launch
+ * stream.  Host-side only; no synchronisation. */
+hive_status hive_profile_enable(hive_table* t, int enable);
+
+/* Accumulates the recorded kernel times into *out (adding to what it holds)
+ * and forgets them.  Synchronises on the recorded events. */
+hive_status hive_profile_read(hive_table* t, hive_profile_t* out);
+
+/* Text of the calling thread's last error (never NULL). */
+const char* hive_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HIVE_H_ */

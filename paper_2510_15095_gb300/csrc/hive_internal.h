@@ -1,0 +1,107 @@
+// Internal interface between the host library (hive_host.cpp) and the kernels
+// (hive_kernels.cu).  Not installed; the public ABI is include/hive.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hive {
+
+constexpr uint32_t kSlots = 32;                    // S, slots per bucket (Section III-A)
+constexpr uint64_t kEmptyWord = ~0ull;             // empty slot: key 0xFFFFFFFF
+constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
+constexpr uint32_t kReservedKeyMin = 0xFFFFFFFEu;  // keys >= this are reserved
+constexpr uint32_t kNoOp = 0xFFFFFFFFu;            // list entry without a caller op
+
+// Sticky error bits in Ctrl::err.
+enum : uint32_t {
+  kErrReserved = 1u << 0,
+  kErrFull = 1u << 1,
+  kErrTimeout = 1u << 2,
+  kErrContract = 1u << 3,
+};
+
+// Counter slots in Ctrl::stats (same order as hive_stats_t).
+enum : int {
+  kStReplaced = 0,
+  kStClaimedFast,
+  kStOverflowed,
+  kStClaimedSlow,
+  kStEvictRounds,
+  kStLockAcquired,
+  kStLockTimeouts,
+  kStStashed,
+  kStPending,
+  kStStashReinserted,
+  kStSplits,
+  kStMerges,
+  kStProbes,
+  kStStashLookups,
+  kNumStats = 16
+};
+
+// Device-resident control block of one table.
+struct alignas(128) Ctrl {
+  unsigned long long size;   // live entries (buckets + stash)
+  unsigned int stash_n;      // sorted, searchable prefix of the stash
+  unsigned int stash_tail;   // append cursor; [stash_n, stash_tail) unsorted
+  unsigned int stash_claims; // appended + reserved by running eviction chains
+  unsigned int stash_dirty;  // a stash word was erased since the last maintenance
+  unsigned int ovf_n;        // entries in the overflow list (P1 -> P2)
+  unsigned int pend_n;       // entries in the pending list (no room found)
+  unsigned int err;          // sticky error bits
+  unsigned int merge_excess; // words a merge batch cannot keep in the low bucket
+  unsigned int n_insert;     // insert ops counted in a mixed batch
+  unsigned int pad0[5];
+  unsigned long long stats[kNumStats];
+};
+
+// Everything a kernel needs to reach one table; passed by value.
+struct View {
+  uint64_t* buckets;     // [nb_max * S] packed words (value << 32 | key)
+  uint32_t* masks;       // [nb_max] free masks, bit i set = slot i free
+  uint32_t* locks;       // [nb_max] bucket locks (eviction only)
+  uint64_t* stash_kv;    // [stash_alloc] stash words, EMPTY padded
+  uint32_t* stash_keys;  // [stash_cap] keys of the sorted prefix
+  Ctrl* ctrl;
+  uint32_t M;            // linear-hashing index mask 2^m - 1
+  uint32_t p;            // split pointer
+  uint32_t nb;           // buckets in use
+  uint32_t stash_cap;    // appends never pass this
+  uint32_t max_evictions;
+  uint32_t lock_spin_limit;
+  uint32_t placement;    // 0 balanced, 1 BitHash1 first
+  uint32_t pad;
+};
+
+// An op list handed from the bulk kernel to the eviction kernel.
+struct List {
+  uint64_t* words;
+  uint32_t* idx;   // caller op index or kNoOp
+  unsigned int* count;
+};
+
+enum OpMode : int { kModeFind = 0, kModeInsert = 1, kModeErase = 2, kModeMixed = 3 };
+
+struct Launch {
+  int num_sms;
+  int ops_blocks_per_sm;
+  int ovf_blocks_per_sm;
+};
+
+// Kernel launchers (hive_kernels.cu).  Each returns the launch error.
+cudaError_t launch_ops(int mode, const View& v, const uint8_t* ops, const uint32_t* keys,
+                       const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
+                       uint8_t* status, List ovf, const Launch& L, cudaStream_t s);
+cudaError_t launch_overflow(const View& v, List in, List pend, int resizable, uint8_t* status,
+                            const Launch& L, cudaStream_t s);
+cudaError_t launch_maintenance(const View& v, cudaStream_t s);
+cudaError_t launch_split(const View& v_new, uint32_t src0, uint32_t count, uint32_t half,
+                         cudaStream_t s);
+cudaError_t launch_merge_excess(const View& v_new, uint32_t count, cudaStream_t s);
+cudaError_t launch_merge(const View& v_new, uint32_t count, List ovf, cudaStream_t s);
+cudaError_t launch_count_inserts(const uint8_t* ops, uint64_t n, unsigned int* out,
+                                 cudaStream_t s);
+cudaError_t query_occupancy(Launch* L);
+
+}  // namespace hive

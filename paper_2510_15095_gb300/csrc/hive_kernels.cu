@@ -1,0 +1,915 @@
+// Hive hash table kernels for GB300 (sm_103a).
+//
+// Layout (Section III-A/B of the paper): a bucket is S = 32 packed 64-bit words
+// (value << 32 | key), 256 bytes, 256-byte aligned; a 32-bit free mask per bucket
+// (bit i set = slot i free); a 32-bit lock per bucket used only by eviction; an
+// overflow stash of packed words.  The empty word is all ones (key 0xFFFFFFFF).
+//
+// Kernels:
+//   k_ops<MODE>   bulk find / insert (steps 1-2) / erase / mixed batch.  A warp
+//                 takes 32 ops; each 16-lane half-warp reads one 256-byte bucket
+//                 as 16-byte fragments, so one load instruction probes two
+//                 buckets.  Match-and-elect (WCME, Section III-F) is a ballot over
+//                 the fragments; the lowest matching lane acts.  New keys claim
+//                 a slot with one atomicAnd on the free mask (WABC, Section
+//                 III-E), the free slot being predicted from the probe itself.
+//   k_overflow    steps 3-4 for inserts whose two buckets were full: warp per
+//                 item, bounded cuckoo eviction under the bucket lock
+//                 (Algorithm 3), then the stash.
+//   k_maint       stash maintenance: reinsert stash words into buckets that
+//                 have room, compact, sort by key (lookups binary-search it).
+//   k_split       linear-hashing expansion, warp per bucket pair (Section IV-C1).
+//   k_merge       linear-hashing contraction, warp per bucket pair (IV-C2).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hive_internal.h"
+
+namespace hive {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kOpsThreads = 256;
+constexpr int kOvfThreads = 256;
+constexpr int kMaintThreads = 1024;
+constexpr unsigned kMaintSmemWords = 8192;  // 64 KB of words sorted in shared memory
+constexpr int kProbeU = 4;                  // load instructions (2 buckets each) in flight
+
+// Per-op status codes (same numbers as include/hive.h).
+enum : uint8_t {
+  ST_INSERTED = 0,
+  ST_REPLACED = 1,
+  ST_ERASED = 2,
+  ST_NOT_FOUND = 3,
+  ST_FOUND = 4,
+  ST_FULL = 5,
+  ST_RESERVED = 6
+};
+enum : uint32_t { OP_INSERT = 0, OP_FIND = 1, OP_ERASE = 2 };
+
+// ----------------------------------------------------------------------------
+// Hashing and addressing
+// ----------------------------------------------------------------------------
+
+// BitHash1 (Section III-C, Listing 1) without the final reduction: a
+// Wang-style shift/xor/multiply avalanche.
+__device__ __forceinline__ uint32_t bithash1(uint32_t k) {
+  uint32_t x = (k << 15) - k - 1u;
+  x = x ^ (x >> 12);
+  x = x + (x << 2);
+  x = x ^ (x >> 4);
+  x = x * 2057u;
+  return x ^ (x >> 16);
+}
+
+// BitHash2 (Section III-C, Listing 1) without the final reduction: Jenkins'
+// six-step add/xor/shift mix.
+__device__ __forceinline__ uint32_t bithash2(uint32_t k) {
+  uint32_t x = k * 4097u + 0x7ED55D16u;
+  x = x ^ (x >> 19) ^ 0xC761C23Cu;
+  x = x * 33u + 0x165667B1u;
+  x = (x + 0xD3A2646Cu) ^ (x << 9);
+  x = x * 9u + 0xFD7046C5u;
+  return x ^ (x >> 16) ^ 0xB55A4F09u;
+}
+
+// Linear-hashing address (Section IV-C): buckets below the split pointer have
+// been split this round and use one more hash bit.
+__device__ __forceinline__ uint32_t lh_bucket(uint32_t h, uint32_t M, uint32_t p) {
+  const uint32_t b = h & M;
+  return b < p ? (h & (2u * M + 1u)) : b;
+}
+
+__device__ __forceinline__ uint64_t pack(uint32_t k, uint32_t v) {
+  return (static_cast<uint64_t>(v) << 32) | k;
+}
+__device__ __forceinline__ uint32_t key_of(uint64_t w) { return static_cast<uint32_t>(w); }
+__device__ __forceinline__ uint32_t val_of(uint64_t w) { return static_cast<uint32_t>(w >> 32); }
+
+// ----------------------------------------------------------------------------
+// Memory access helpers
+// ----------------------------------------------------------------------------
+
+// 16-byte bucket fragment through the read-only path (table not written by
+// the running kernel).
+__device__ __forceinline__ void ld_frag_ro(const uint64_t* p, uint64_t& a, uint64_t& b) {
+  asm("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
+}
+// 16-byte bucket fragment while other warps may be writing the table.
+__device__ __forceinline__ void ld_frag(const uint64_t* p, uint64_t& a, uint64_t& b) {
+  asm volatile("ld.relaxed.gpu.global.L1::no_allocate.v2.u64 {%0, %1}, [%2];"
+               : "=l"(a), "=l"(b)
+               : "l"(p)
+               : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed64(const uint64_t* p) {
+  uint64_t r;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(r) : "l"(p) : "memory");
+  return r;
+}
+__device__ __forceinline__ uint32_t ld_relaxed32(const uint32_t* p) {
+  uint32_t r;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");
+  return r;
+}
+__device__ __forceinline__ void st_relaxed64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long* ull(uint64_t* p) {
+  return reinterpret_cast<unsigned long long*>(p);
+}
+
+// ----------------------------------------------------------------------------
+// Slot claims (WABC, Section III-E / Algorithm 2)
+// ----------------------------------------------------------------------------
+
+// Claim a free slot of bucket b starting from the predicted slot `s`, then
+// publish `word` with a plain store.  Used where no eviction runs concurrently
+// (the bulk kernel and maintenance).  Algorithm 2 restores the bit with
+// fetch_or when the fetch_and finds it already clear; that would free a slot
+// another warp owns, so here a failed claim retries on the returned mask.
+__device__ __forceinline__ bool claim_store(const View& v, uint32_t b, uint32_t s,
+                                            uint64_t word) {
+  for (int t = 0; t <= static_cast<int>(kSlots) && s < kSlots; ++t) {
+    const uint32_t bit = 1u << s;
+    const uint32_t old = atomicAnd(v.masks + b, ~bit);
+    if (old & bit) {
+      st_relaxed64(v.buckets + static_cast<uint64_t>(b) * kSlots + s, word);
+      return true;
+    }
+    s = old ? static_cast<uint32_t>(__ffs(old) - 1) : kSlots;
+  }
+  return false;
+}
+
+// Claim for the eviction phase: publish with CAS(EMPTY -> word).  An evictor
+// holding the bucket lock may exchange a claimed-but-unpublished slot (it then
+// reads EMPTY as its victim and stops); the CAS then fails and this claim
+// looks for another bit.  Bits only get cleared in this phase, so the loop
+// ends after at most S successful fetch_ands.
+__device__ __forceinline__ bool claim_cas(const View& v, uint32_t b, uint64_t word) {
+  uint32_t fm = ld_relaxed32(v.masks + b);
+  for (int t = 0; t <= 2 * static_cast<int>(kSlots) && fm; ++t) {
+    const uint32_t s = __ffs(fm) - 1;
+    const uint32_t bit = 1u << s;
+    const uint32_t old = atomicAnd(v.masks + b, ~bit);
+    if (old & bit) {
+      unsigned long long* sp = ull(v.buckets + static_cast<uint64_t>(b) * kSlots + s);
+      if (atomicCAS(sp, kEmptyWord, word) == kEmptyWord) return true;
+      fm = ld_relaxed32(v.masks + b);
+    } else {
+      fm = old;
+    }
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool lock_bucket(const View& v, uint32_t b) {
+  for (uint32_t t = 0; t < v.lock_spin_limit; ++t) {
+    if (atomicCAS(v.locks + b, 0u, 1u) == 0u) {
+      __threadfence();
+      return true;
+    }
+    __nanosleep(64);
+  }
+  return false;
+}
+__device__ __forceinline__ void unlock_bucket(const View& v, uint32_t b) {
+  __threadfence();
+  atomicExch(v.locks + b, 0u);
+}
+
+// Stash binary search over the sorted key prefix.
+__device__ __forceinline__ bool stash_find(const View& v, uint32_t stash_n, uint32_t key,
+                                           uint32_t& pos) {
+  uint32_t lo = 0, hi = stash_n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(v.stash_keys + mid) < key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  pos = lo;
+  return lo < stash_n && __ldg(v.stash_keys + lo) == key;
+}
+
+// ----------------------------------------------------------------------------
+// Bulk op kernel
+// ----------------------------------------------------------------------------
+
+struct LaneCounters {
+  int size_delta = 0;
+  unsigned replaced = 0, claimed = 0, overflowed = 0, stash_lookups = 0;
+  unsigned long long probes = 0;  // warp-uniform: buckets probed by this warp
+  bool reserved = false, contract = false;
+};
+
+// One probe round: for every op whose bit is set in `need`, read bucket `myb`
+// of that op (the value held by the op's home lane) and match-and-elect.
+// Results land in the home lane: done/status/value, or for inserts the free
+// count and first free slot of the bucket.
+template <int MODE>
+__device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb, uint32_t key,
+                                      uint32_t val, uint32_t op, int lane, bool& done,
+                                      uint8_t& st, uint32_t& outv, uint32_t& fcnt,
+                                      uint32_t& fslot, LaneCounters& cnt) {
+  constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
+  const int half = lane >> 4;
+  const int hl = lane & 15;
+  while (need) {
+    int oa[kProbeU], ob[kProbeU];
+#pragma unroll
+    for (int u = 0; u < kProbeU; ++u) {
+      oa[u] = need ? __ffs(need) - 1 : -1;
+      need &= need - 1u;
+      ob[u] = need ? __ffs(need) - 1 : -1;
+      need &= need - 1u;
+    }
+    uint64_t wa[kProbeU], wb[kProbeU];
+    uint32_t kq[kProbeU], bq[kProbeU], vq[kProbeU], oq[kProbeU];
+#pragma unroll
+    for (int u = 0; u < kProbeU; ++u) {
+      const int o = half ? ob[u] : oa[u];
+      const int src = o & 31;
+      bq[u] = __shfl_sync(kFull, myb, src);
+      kq[u] = __shfl_sync(kFull, key, src);
+      vq[u] = kIns ? __shfl_sync(kFull, val, src) : 0u;
+      oq[u] = (MODE == kModeMixed) ? __shfl_sync(kFull, op, src) : 0u;
+      if (o >= 0) {
+        const uint64_t* p = v.buckets + static_cast<uint64_t>(bq[u]) * kSlots + 2 * hl;
+        if (MODE == kModeFind)
+          ld_frag_ro(p, wa[u], wb[u]);
+        else
+          ld_frag(p, wa[u], wb[u]);
+      } else {
+        wa[u] = kEmptyWord;
+        wb[u] = kEmptyWord;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kProbeU; ++u) {
+      const bool lo = key_of(wa[u]) == kq[u];
+      const bool hi = key_of(wb[u]) == kq[u];
+      const unsigned m = __ballot_sync(kFull, lo || hi);
+      unsigned elo = 0, ehi = 0;
+      if (kIns) {
+        elo = __ballot_sync(kFull, wa[u] == kEmptyWord);
+        ehi = __ballot_sync(kFull, wb[u] == kEmptyWord);
+      }
+      // The elected lane's result: the value for a find, CAS success otherwise.
+      uint32_t res = lo ? val_of(wa[u]) : val_of(wb[u]);
+      if (MODE != kModeFind && (lo || hi)) {
+        const int my_o = half ? ob[u] : oa[u];
+        const unsigned hm_mine = (m >> (16 * half)) & 0xFFFFu;
+        if (my_o >= 0 && hl == __ffs(hm_mine) - 1) {
+          const uint32_t opk =
+              MODE == kModeMixed ? oq[u] : (MODE == kModeErase ? OP_ERASE : OP_INSERT);
+          const uint32_t slot = 2 * hl + (lo ? 0 : 1);
+          uint64_t* sp = v.buckets + static_cast<uint64_t>(bq[u]) * kSlots + slot;
+          const uint64_t cur = lo ? wa[u] : wb[u];
+          if (opk == OP_ERASE) {
+            // Algorithm 4: CAS the slot to EMPTY, then publish the free bit.
+            res = atomicCAS(ull(sp), cur, kEmptyWord) == cur;
+            if (res) {
+              __threadfence();
+              atomicOr(v.masks + bq[u], 1u << slot);
+            }
+          } else if (opk == OP_INSERT) {
+            // Algorithm 1: CAS the cached word to the new pair.
+            res = atomicCAS(ull(sp), cur, pack(kq[u], vq[u])) == cur;
+          }
+        }
+      }
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        const int o = hf ? ob[u] : oa[u];
+        if (o < 0) continue;
+        const unsigned hm = (m >> (16 * hf)) & 0xFFFFu;
+        if (hm) {
+          const int w = 16 * hf + __ffs(hm) - 1;
+          const uint32_t r = __shfl_sync(kFull, res, w);
+          if (lane == o) {
+            done = true;
+            const uint32_t opk =
+                MODE == kModeMixed ? op : (MODE == kModeFind ? OP_FIND : (MODE == kModeErase ? OP_ERASE : OP_INSERT));
+            if (opk == OP_FIND) {
+              outv = r;
+              st = ST_FOUND;
+            } else if (opk == OP_ERASE) {
+              st = ST_ERASED;
+              if (r) cnt.size_delta -= 1; else cnt.contract = true;
+            } else {
+              st = ST_REPLACED;
+              if (r) cnt.replaced += 1; else cnt.contract = true;
+            }
+          }
+        } else if (kIns) {
+          const unsigned ev = (elo >> (16 * hf)) & 0xFFFFu;
+          const unsigned od = (ehi >> (16 * hf)) & 0xFFFFu;
+          if (lane == o) {
+            fcnt = __popc(ev) + __popc(od);
+            const uint32_t se = ev ? 2u * (__ffs(ev) - 1) : kSlots;
+            const uint32_t so = od ? 2u * (__ffs(od) - 1) + 1u : kSlots;
+            fslot = se < so ? se : so;
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kOpsThreads)
+    k_ops(View v, const uint8_t* __restrict__ ops, const uint32_t* __restrict__ keys,
+          const uint32_t* __restrict__ vals, uint64_t n, uint32_t* __restrict__ vals_out,
+          uint8_t* __restrict__ found, uint8_t* __restrict__ status, List ovf) {
+  constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp0 = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  const uint64_t nchunks = (n + 31) >> 5;
+  const uint32_t stash_n = v.ctrl->stash_n;
+  LaneCounters cnt;
+
+  for (uint64_t c = warp0; c < nchunks; c += nwarps) {
+    const uint64_t i = (c << 5) + lane;
+    const bool valid = i < n;
+    uint32_t op = OP_FIND;
+    if (MODE == kModeMixed)
+      op = valid ? static_cast<uint32_t>(__ldcs(ops + i)) : OP_FIND;
+    else if (MODE == kModeInsert)
+      op = OP_INSERT;
+    else if (MODE == kModeErase)
+      op = OP_ERASE;
+    if (op > OP_ERASE) op = OP_FIND;  // unknown op codes read only
+    const uint32_t key = valid ? __ldcs(keys + i) : kEmptyKey;
+    uint32_t val = 0;
+    if (kIns && valid && op == OP_INSERT && vals) val = __ldcs(vals + i);
+    const bool reserved = valid && key >= kReservedKeyMin;
+    const bool live = valid && !reserved;
+    cnt.reserved |= reserved;
+
+    const uint32_t b1 = lh_bucket(bithash1(key), v.M, v.p);
+    const uint32_t b2 = lh_bucket(bithash2(key), v.M, v.p);
+    bool done = !live;
+    uint8_t st = reserved ? ST_RESERVED : ST_NOT_FOUND;
+    uint32_t outv = 0;
+    uint32_t f1 = 0, s1 = kSlots, f2 = 0, s2 = kSlots;
+
+    // Probe the BitHash1 bucket of every op, then the BitHash2 bucket of the
+    // ops still unresolved (Section IV-B: WCME over the d = 2 candidates).
+    unsigned need = __ballot_sync(kFull, !done);
+    cnt.probes += __popc(need);
+    if (need) probe<MODE>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt);
+    need = __ballot_sync(kFull, !done);
+    cnt.probes += __popc(need);
+    if (need) probe<MODE>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt);
+
+    // The stash (Section IV-A step 4) holds keys that found no bucket room.
+    if (!done && stash_n) {
+      uint32_t pos;
+      cnt.stash_lookups += 1;
+      if (stash_find(v, stash_n, key, pos)) {
+        uint64_t* sp = v.stash_kv + pos;
+        const uint64_t w = ld_relaxed64(sp);
+        if (key_of(w) == key) {
+          done = true;
+          if (op == OP_FIND) {
+            outv = val_of(w);
+            st = ST_FOUND;
+          } else if (op == OP_ERASE) {
+            st = ST_ERASED;
+            if (atomicCAS(ull(sp), w, kEmptyWord) == w) {
+              cnt.size_delta -= 1;
+              atomicExch(&v.ctrl->stash_dirty, 1u);
+            } else {
+              cnt.contract = true;
+            }
+          } else {
+            st = ST_REPLACED;
+            if (atomicCAS(ull(sp), w, pack(key, val)) == w) cnt.replaced += 1; else cnt.contract = true;
+          }
+        }
+      }
+    }
+
+    // Step 2: claim-then-commit for absent keys.
+    bool to_ovf = false;
+    if (kIns && !done && op == OP_INSERT) {
+      const uint64_t word = pack(key, val);
+      const bool first1 = v.placement ? (f1 > 0) : (f1 >= f2);
+      const uint32_t tb = first1 ? b1 : b2, ts = first1 ? s1 : s2;
+      const uint32_t ob = first1 ? b2 : b1, os = first1 ? s2 : s1;
+      bool placed = false;
+      if (f1 + f2 > 0) {
+        placed = claim_store(v, tb, ts, word);
+        if (!placed && ob != tb) placed = claim_store(v, ob, os, word);
+      }
+      if (placed) {
+        done = true;
+        st = ST_INSERTED;
+        cnt.size_delta += 1;
+        cnt.claimed += 1;
+      } else {
+        to_ovf = true;
+        cnt.overflowed += 1;
+      }
+    }
+
+    // Hand full-bucket inserts to the eviction kernel (steps 3-4).
+    if (kIns) {
+      const unsigned om = __ballot_sync(kFull, to_ovf);
+      if (om) {
+        const int leader = __ffs(om) - 1;
+        unsigned base = 0;
+        if (lane == leader) base = atomicAdd(ovf.count, static_cast<unsigned>(__popc(om)));
+        base = __shfl_sync(kFull, base, leader);
+        if (to_ovf) {
+          const unsigned r = base + __popc(om & ((1u << lane) - 1u));
+          ovf.words[r] = pack(key, val);
+          ovf.idx[r] = static_cast<uint32_t>(i);
+        }
+      }
+    }
+
+    if (valid) {
+      if (MODE == kModeFind) {
+        __stcs(vals_out + i, outv);
+        if (found) found[i] = st == ST_FOUND ? 1 : 0;
+      } else {
+        if (status && !to_ovf) status[i] = st;
+        if (MODE == kModeMixed && vals_out) __stcs(vals_out + i, outv);
+      }
+    }
+  }
+
+  // One atomic per warp per counter.
+  const int sd = __reduce_add_sync(kFull, static_cast<unsigned>(cnt.size_delta));
+  const unsigned rp = __reduce_add_sync(kFull, cnt.replaced);
+  const unsigned cl = __reduce_add_sync(kFull, cnt.claimed);
+  const unsigned of = __reduce_add_sync(kFull, cnt.overflowed);
+  const unsigned rs = __ballot_sync(kFull, cnt.reserved);
+  const unsigned ct = __ballot_sync(kFull, cnt.contract);
+  const unsigned sl = __reduce_add_sync(kFull, cnt.stash_lookups);
+  if (lane == 0) {
+    if (cnt.probes) atomicAdd(&v.ctrl->stats[kStProbes], cnt.probes);
+    if (sl) atomicAdd(&v.ctrl->stats[kStStashLookups], static_cast<unsigned long long>(sl));
+    if (sd) atomicAdd(&v.ctrl->size, static_cast<unsigned long long>(static_cast<long long>(sd)));
+    if (rp) atomicAdd(&v.ctrl->stats[kStReplaced], static_cast<unsigned long long>(rp));
+    if (cl) atomicAdd(&v.ctrl->stats[kStClaimedFast], static_cast<unsigned long long>(cl));
+    if (of) atomicAdd(&v.ctrl->stats[kStOverflowed], static_cast<unsigned long long>(of));
+    if (rs) atomicOr(&v.ctrl->err, kErrReserved);
+    if (ct) atomicOr(&v.ctrl->err, kErrContract);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Steps 3-4: bounded cuckoo eviction and the overflow stash (Algorithm 3)
+// ----------------------------------------------------------------------------
+
+// A chain may end in the stash, so it first reserves a stash word; chains that
+// finish in a bucket give the reservation back, so appends never pass
+// stash_cap.  When every free word is reserved by running chains, wait for
+// them (they end within max_evictions rounds); give up only once the stash is
+// really full or after a bounded wait.
+__device__ __forceinline__ bool stash_reserve(const View& v) {
+  const uint32_t limit = v.lock_spin_limit * 4u;
+  for (uint32_t t = 0; t < limit; ++t) {
+    const unsigned c = atomicAdd(&v.ctrl->stash_claims, 1u);
+    if (c < v.stash_cap) return true;
+    atomicSub(&v.ctrl->stash_claims, 1u);
+    if (ld_relaxed32(&v.ctrl->stash_tail) >= v.stash_cap) return false;
+    __nanosleep(256);
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kOvfThreads)
+    k_overflow(View v, List in, List pend, int resizable, uint8_t* __restrict__ status) {
+  const int lane = threadIdx.x & 31;
+  const unsigned warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  const unsigned total = *in.count;
+  unsigned c_claim = 0, c_rounds = 0, c_locks = 0, c_to = 0, c_stash = 0, c_pend = 0, c_new = 0;
+
+  for (unsigned it = warp0; it < total; it += nwarps) {
+    const uint64_t word0 = in.words[it];
+    const uint32_t idx = in.idx[it];
+    const uint32_t key0 = key_of(word0);
+    const uint32_t b1 = lh_bucket(bithash1(key0), v.M, v.p);
+    const uint32_t b2 = lh_bucket(bithash2(key0), v.M, v.p);
+
+    // 0: needs eviction, 1: placed, 2: stashed, 3: no room (pending)
+    int outcome = 0;
+    if (lane == 0) {
+      if (claim_cas(v, b1, word0) || (b2 != b1 && claim_cas(v, b2, word0))) {
+        outcome = 1;
+        ++c_claim;
+      } else if (!stash_reserve(v)) {
+        outcome = 3;
+      }
+    }
+    outcome = __shfl_sync(kFull, outcome, 0);
+
+    if (outcome == 0) {
+      uint64_t cur = word0;
+      uint32_t b = b1;
+      bool placed = false;
+      for (uint32_t r = 0; r < v.max_evictions; ++r) {
+        // Look ahead: each lane checks whether the word in its slot could move
+        // to its other candidate bucket without a further eviction.
+        const uint64_t w = ld_relaxed64(v.buckets + static_cast<uint64_t>(b) * kSlots + lane);
+        bool good = false;
+        if (w != kEmptyWord) {
+          const uint32_t k = key_of(w);
+          const uint32_t a1 = lh_bucket(bithash1(k), v.M, v.p);
+          const uint32_t a2 = lh_bucket(bithash2(k), v.M, v.p);
+          const uint32_t alt = (a1 == b) ? a2 : a1;
+          if (alt != b) good = ld_relaxed32(v.masks + alt) != 0u;
+        }
+        const unsigned gm = __ballot_sync(kFull, good);
+        int res = 0;  // 0: evicted `victim`, 1: placed, 2: lock wait gave up
+        uint64_t victim = kEmptyWord;
+        if (lane == 0) {
+          ++c_rounds;
+          const uint32_t vs = gm ? static_cast<uint32_t>(__ffs(gm) - 1)
+                                 : ((bithash2(key_of(cur)) + r) & (kSlots - 1));
+          if (!lock_bucket(v, b)) {
+            res = 2;
+            ++c_to;
+          } else {
+            ++c_locks;
+            if (claim_cas(v, b, cur)) {
+              res = 1;
+            } else {
+              victim = atomicExch(ull(v.buckets + static_cast<uint64_t>(b) * kSlots + vs), cur);
+              res = (victim == kEmptyWord) ? 1 : 0;
+            }
+            unlock_bucket(v, b);
+          }
+        }
+        res = __shfl_sync(kFull, res, 0);
+        victim = __shfl_sync(kFull, victim, 0);
+        if (res == 1) {
+          placed = true;
+          break;
+        }
+        if (res == 2) break;
+        // Re-route the displaced word to its alternate bucket.
+        cur = victim;
+        const uint32_t kc = key_of(cur);
+        const uint32_t a1 = lh_bucket(bithash1(kc), v.M, v.p);
+        const uint32_t a2 = lh_bucket(bithash2(kc), v.M, v.p);
+        const uint32_t nb = (a1 == b) ? a2 : a1;
+        if (nb == b) break;  // both candidates are this bucket: no alternative
+        b = nb;
+        int ok = 0;
+        if (lane == 0) ok = claim_cas(v, b, cur);
+        if (__shfl_sync(kFull, ok, 0)) {
+          placed = true;
+          break;
+        }
+      }
+      if (lane == 0) {
+        if (placed) {
+          atomicSub(&v.ctrl->stash_claims, 1u);
+        } else {
+          const unsigned pos = atomicAdd(&v.ctrl->stash_tail, 1u);
+          st_relaxed64(v.stash_kv + pos, cur);
+          ++c_stash;
+        }
+      }
+      outcome = placed ? 1 : 2;
+    }
+
+    if (lane == 0) {
+      if (outcome == 3) {
+        ++c_pend;
+        if (resizable) {
+          const unsigned pos = atomicAdd(pend.count, 1u);
+          pend.words[pos] = word0;
+          pend.idx[pos] = idx;
+        } else {
+          atomicOr(&v.ctrl->err, kErrFull);
+          if (status && idx != kNoOp) status[idx] = ST_FULL;
+        }
+      } else if (idx != kNoOp) {
+        ++c_new;
+        if (status) status[idx] = ST_INSERTED;
+      }
+    }
+  }
+
+  if (lane == 0) {
+    Ctrl* c = v.ctrl;
+    if (c_new) atomicAdd(&c->size, static_cast<unsigned long long>(c_new));
+    if (c_claim) atomicAdd(&c->stats[kStClaimedSlow], static_cast<unsigned long long>(c_claim));
+    if (c_rounds) atomicAdd(&c->stats[kStEvictRounds], static_cast<unsigned long long>(c_rounds));
+    if (c_locks) atomicAdd(&c->stats[kStLockAcquired], static_cast<unsigned long long>(c_locks));
+    if (c_to) {
+      atomicAdd(&c->stats[kStLockTimeouts], static_cast<unsigned long long>(c_to));
+      atomicOr(&c->err, kErrTimeout);
+    }
+    if (c_stash) atomicAdd(&c->stats[kStStashed], static_cast<unsigned long long>(c_stash));
+    if (c_pend) atomicAdd(&c->stats[kStPending], static_cast<unsigned long long>(c_pend));
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Stash maintenance (single CTA)
+// ----------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t sort_key(uint64_t w) { return key_of(w); }
+
+// Bitonic sort of a[0, P) by key (P a power of two), one CTA.
+__device__ void block_bitonic(uint64_t* a, unsigned P) {
+  for (unsigned k = 2; k <= P; k <<= 1) {
+    for (unsigned j = k >> 1; j > 0; j >>= 1) {
+      for (unsigned t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
+        const unsigned low = t & (j - 1);
+        const unsigned i = ((t - low) << 1) | low;
+        const unsigned l = i | j;
+        const uint64_t x = a[i], y = a[l];
+        const bool up = (i & k) == 0;
+        if ((sort_key(x) > sort_key(y)) == up) {
+          a[i] = y;
+          a[l] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kMaintThreads) k_maint(View v) {
+  extern __shared__ uint64_t smem[];
+  __shared__ unsigned s_reins, s_live;
+  Ctrl* c = v.ctrl;
+  const unsigned tail = c->stash_tail;
+  const unsigned sorted = c->stash_n;
+  const unsigned dirty = c->stash_dirty;
+  if (threadIdx.x == 0) {
+    s_reins = 0;
+    s_live = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) c->ovf_n = 0;  // the next call's overflow list starts empty
+  if (tail == sorted && !dirty) return;
+
+  // Move stash words back into a candidate bucket that has room.
+  unsigned reins = 0;
+  for (unsigned j = threadIdx.x; j < tail; j += blockDim.x) {
+    const uint64_t w = v.stash_kv[j];
+    if (w == kEmptyWord) continue;
+    const uint32_t k = key_of(w);
+    const uint32_t b1 = lh_bucket(bithash1(k), v.M, v.p);
+    const uint32_t b2 = lh_bucket(bithash2(k), v.M, v.p);
+    const uint32_t m1 = ld_relaxed32(v.masks + b1);
+    bool ok = m1 && claim_store(v, b1, __ffs(m1) - 1, w);
+    if (!ok) {
+      const uint32_t m2 = ld_relaxed32(v.masks + b2);
+      ok = m2 && claim_store(v, b2, __ffs(m2) - 1, w);
+    }
+    if (ok) {
+      v.stash_kv[j] = kEmptyWord;
+      ++reins;
+    }
+  }
+  if (reins) atomicAdd(&s_reins, reins);
+  __syncthreads();
+
+  unsigned P = 1;
+  while (P < tail) P <<= 1;
+  if (P <= kMaintSmemWords) {
+    for (unsigned j = threadIdx.x; j < P; j += blockDim.x) smem[j] = j < tail ? v.stash_kv[j] : kEmptyWord;
+    __syncthreads();
+    block_bitonic(smem, P);
+    for (unsigned j = threadIdx.x; j < P; j += blockDim.x) v.stash_kv[j] = smem[j];
+  } else {
+    // [tail, P) is EMPTY by construction: the buffer is a power of two long
+    // and every word past the live prefix is reset to EMPTY below.
+    block_bitonic(v.stash_kv, P);
+  }
+  __syncthreads();
+
+  // EMPTY words sort last: the live prefix ends at the first EMPTY word.
+  unsigned live = 0;
+  for (unsigned j = threadIdx.x; j < P; j += blockDim.x) {
+    const uint64_t w = v.stash_kv[j];
+    if (w != kEmptyWord) {
+      v.stash_keys[j] = key_of(w);
+      ++live;
+    }
+  }
+  if (live) atomicAdd(&s_live, live);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c->stash_n = s_live;
+    c->stash_tail = s_live;
+    c->stash_claims = s_live;
+    c->stash_dirty = 0;
+    if (s_reins) c->stats[kStStashReinserted] += s_reins;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Linear-hashing resize (Section IV-C)
+// ----------------------------------------------------------------------------
+
+// Expansion: warp w splits bucket src0 + w into its partner src0 + w + half.
+// `v` carries the state after this launch.  A word leaves the source bucket
+// when neither candidate address equals the source under the new state; it
+// then belongs to the partner, where the movers are packed from slot 0 by a
+// ballot-rank compaction.
+__global__ void __launch_bounds__(256) k_split(View v, uint32_t src0, uint32_t count, uint32_t half) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= count) return;
+  const uint32_t src = src0 + w;
+  const uint32_t dst = src + half;
+  uint64_t* sb = v.buckets + static_cast<uint64_t>(src) * kSlots;
+  uint64_t* db = v.buckets + static_cast<uint64_t>(dst) * kSlots;
+  const uint64_t word = sb[lane];
+  bool mv = false;
+  if (word != kEmptyWord) {
+    const uint32_t k = key_of(word);
+    const uint32_t a1 = lh_bucket(bithash1(k), v.M, v.p);
+    const uint32_t a2 = lh_bucket(bithash2(k), v.M, v.p);
+    mv = (a1 != src) && (a2 != src);
+  }
+  const unsigned mm = __ballot_sync(kFull, mv);
+  if (mv) {
+    db[__popc(mm & ((1u << lane) - 1u))] = word;
+    sb[lane] = kEmptyWord;
+  }
+  if (lane == 0) {
+    v.masks[src] |= mm;
+    const int nm = __popc(mm);
+    v.masks[dst] = nm >= 32 ? 0u : (0xFFFFFFFFu << nm);
+  }
+}
+
+// Contraction pre-check: how many words of the batch's high buckets do not
+// fit into the free slots of their low partner.
+__global__ void __launch_bounds__(256) k_merge_excess(View v, uint32_t count) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= count) return;
+  const uint32_t low = v.p + w;
+  const uint32_t high = low + v.M + 1u;
+  const uint64_t word = v.buckets[static_cast<uint64_t>(high) * kSlots + lane];
+  const int live = __popc(__ballot_sync(kFull, word != kEmptyWord));
+  const int fr = __popc(v.masks[low]);
+  if (lane == 0 && live > fr) atomicAdd(&v.ctrl->merge_excess, static_cast<unsigned>(live - fr));
+}
+
+// Contraction: warp w merges high bucket (p + w + 2^m) into low bucket p + w,
+// `v` carrying the state after this launch.  Live words take the free slots
+// of the low bucket in rank order (select the r-th free bit); words that do
+// not fit go to the overflow list and are placed by the eviction kernel.
+__global__ void __launch_bounds__(256) k_merge(View v, uint32_t count, List ovf) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= count) return;
+  const uint32_t low = v.p + w;
+  const uint32_t high = low + v.M + 1u;
+  uint64_t* lb = v.buckets + static_cast<uint64_t>(low) * kSlots;
+  uint64_t* hb = v.buckets + static_cast<uint64_t>(high) * kSlots;
+  const uint64_t word = hb[lane];
+  const bool live = word != kEmptyWord;
+  const unsigned lm = __ballot_sync(kFull, live);
+  const unsigned rank = __popc(lm & ((1u << lane) - 1u));
+  const uint32_t fr = v.masks[low];
+  const unsigned nfree = __popc(fr);
+  const bool fits = live && rank < nfree;
+  if (fits) {
+    uint32_t m = fr;
+    for (unsigned t = 0; t < rank; ++t) m &= m - 1u;
+    lb[__ffs(m) - 1] = word;
+  }
+  const bool spill = live && !fits;
+  const unsigned sm = __ballot_sync(kFull, spill);
+  if (sm) {
+    const int leader = __ffs(sm) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(ovf.count, static_cast<unsigned>(__popc(sm)));
+    base = __shfl_sync(kFull, base, leader);
+    if (spill) {
+      const unsigned r = base + __popc(sm & ((1u << lane) - 1u));
+      ovf.words[r] = word;
+      ovf.idx[r] = kNoOp;
+    }
+  }
+  hb[lane] = kEmptyWord;
+  if (lane == 0) {
+    const unsigned used = __popc(lm) < nfree ? __popc(lm) : nfree;
+    uint32_t m = fr;
+    for (unsigned t = 0; t < used; ++t) m &= m - 1u;
+    v.masks[low] = m;
+    v.masks[high] = 0xFFFFFFFFu;
+  }
+}
+
+__global__ void k_count_inserts(const uint8_t* __restrict__ ops, uint64_t n, unsigned* out) {
+  unsigned c = 0;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+    c += ops[i] == OP_INSERT;
+  c = __reduce_add_sync(kFull, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+template <int MODE>
+cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys,
+                         const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
+                         uint8_t* status, List ovf, const Launch& L, cudaStream_t s) {
+  const uint64_t chunks = (n + 31) / 32;
+  const uint64_t warps_per_block = kOpsThreads / 32;
+  uint64_t blocks = (chunks + warps_per_block - 1) / warps_per_block;
+  const uint64_t cap = static_cast<uint64_t>(L.num_sms) * L.ops_blocks_per_sm;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  k_ops<MODE><<<static_cast<unsigned>(blocks), kOpsThreads, 0, s>>>(v, ops, keys, vals, n,
+                                                                     vals_out, found, status, ovf);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_ops(int mode, const View& v, const uint8_t* ops, const uint32_t* keys,
+                       const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
+                       uint8_t* status, List ovf, const Launch& L, cudaStream_t s) {
+  switch (mode) {
+    case kModeFind:
+      return launch_ops_t<kModeFind>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
+    case kModeInsert:
+      return launch_ops_t<kModeInsert>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
+    case kModeErase:
+      return launch_ops_t<kModeErase>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
+    default:
+      return launch_ops_t<kModeMixed>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
+  }
+}
+
+cudaError_t launch_overflow(const View& v, List in, List pend, int resizable, uint8_t* status,
+                            const Launch& L, cudaStream_t s) {
+  const unsigned blocks = static_cast<unsigned>(L.num_sms * L.ovf_blocks_per_sm);
+  k_overflow<<<blocks, kOvfThreads, 0, s>>>(v, in, pend, resizable, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maintenance(const View& v, cudaStream_t s) {
+  k_maint<<<1, kMaintThreads, kMaintSmemWords * sizeof(uint64_t), s>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split(const View& v_new, uint32_t src0, uint32_t count, uint32_t half,
+                         cudaStream_t s) {
+  if (!count) return cudaSuccess;
+  const unsigned blocks = (count * 32u + 255u) / 256u;
+  k_split<<<blocks, 256, 0, s>>>(v_new, src0, count, half);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_excess(const View& v_new, uint32_t count, cudaStream_t s) {
+  if (!count) return cudaSuccess;
+  const unsigned blocks = (count * 32u + 255u) / 256u;
+  k_merge_excess<<<blocks, 256, 0, s>>>(v_new, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const View& v_new, uint32_t count, List ovf, cudaStream_t s) {
+  if (!count) return cudaSuccess;
+  const unsigned blocks = (count * 32u + 255u) / 256u;
+  k_merge<<<blocks, 256, 0, s>>>(v_new, count, ovf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_inserts(const uint8_t* ops, uint64_t n, unsigned* out, cudaStream_t s) {
+  if (!n) return cudaSuccess;
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_count_inserts<<<static_cast<unsigned>(blocks), 256, 0, s>>>(ops, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t query_occupancy(Launch* L) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&L->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  int b = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeInsert>, kOpsThreads, 0);
+  if (e != cudaSuccess) return e;
+  L->ops_blocks_per_sm = b > 0 ? b : 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_overflow, kOvfThreads, 0);
+  if (e != cudaSuccess) return e;
+  L->ovf_blocks_per_sm = b > 0 ? (b < 2 ? b : 2) : 1;
+  return cudaFuncSetAttribute(k_maint, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kMaintSmemWords * sizeof(uint64_t)));
+}
+
+}  // namespace hive

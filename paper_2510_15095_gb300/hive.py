@@ -1,0 +1,303 @@
+"""Python binding of the Hive hash table C ABI (include/hive.h).
+
+Argument marshalling only: every step of every operation runs in the CUDA
+kernels of ``libhive_gb300.so``.  Tensors are PyTorch CUDA tensors (PyTorch is
+used for device memory and streams); keys and values are 32-bit (``torch.int32``
+or ``torch.uint32`` storage, reinterpreted as unsigned), per-op codes and
+statuses are ``torch.uint8``.  There is no CPU fallback: if the library is not
+built, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhive_gb300.so")
+
+# Status codes (include/hive.h)
+HIVE_OK = 0
+ERRORS = {1: "INVALID_ARG", 2: "RESERVED_KEY", 3: "OOM", 4: "FULL", 5: "TIMEOUT", 6: "CUDA",
+          7: "CONTRACT"}
+INSERTED, REPLACED, ERASED, NOT_FOUND, FOUND, FULL, RESERVED_KEY = range(7)
+OP_INSERT, OP_FIND, OP_ERASE = 0, 1, 2
+PLACE_BALANCED, PLACE_FIRST = 0, 1
+
+EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", "hive_find",
+           "hive_erase", "hive_execute", "hive_size", "hive_capacity", "hive_clear", "hive_check",
+           "hive_stats", "hive_dump", "hive_profile_enable", "hive_profile_read",
+           "hive_last_error"]
+KERNEL_KINDS = ["find", "insert", "erase", "mixed", "evict", "maint", "split", "merge", "count"]
+
+
+class HiveError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hive error {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("initial_slots", C.c_uint64), ("max_slots", C.c_uint64),
+                ("bucket_slots", C.c_uint32), ("max_evictions", C.c_uint32),
+                ("resize_batch", C.c_uint32), ("stash_permille", C.c_uint32),
+                ("grow_num", C.c_uint32), ("grow_den", C.c_uint32),
+                ("shrink_num", C.c_uint32), ("shrink_den", C.c_uint32),
+                ("resizable", C.c_uint32), ("placement", C.c_uint32),
+                ("lock_spin_limit", C.c_uint32), ("reserved0", C.c_uint32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in (
+        "replaced", "claimed_fast", "overflowed", "claimed_slow", "evict_rounds", "lock_acquired",
+        "lock_timeouts", "stashed", "pending", "stash_reinserted", "splits", "merges", "probes",
+        "stash_lookups")]
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 16), ("launches", C.c_uint64 * 16)]
+
+
+class Image(C.Structure):
+    _fields_ = [("nb", C.c_uint64), ("S", C.c_uint32), ("M", C.c_uint32), ("p", C.c_uint32),
+                ("reserved0", C.c_uint32), ("stash_n", C.c_uint64), ("stash_cap", C.c_uint64),
+                ("size", C.c_uint64), ("pending", C.c_uint64),
+                ("buckets", C.c_void_p), ("masks", C.c_void_p), ("locks", C.c_void_p),
+                ("stash", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhive_gb300.so and declare its signatures.  Raises if missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built; run __graft_entry__.build() "
+                               "(the CUDA library is required, there is no fallback)")
+        L = C.CDLL(path)
+        vp, u64, i32 = C.c_void_p, C.c_uint64, C.c_int
+        L.hive_config_default.argtypes = [C.POINTER(Config)]
+        L.hive_config_default.restype = None
+        L.hive_create.argtypes = [C.POINTER(Config), vp, C.POINTER(vp)]
+        L.hive_destroy.argtypes = [vp]
+        L.hive_insert.argtypes = [vp, vp, vp, u64, vp, vp]
+        L.hive_find.argtypes = [vp, vp, u64, vp, vp, vp]
+        L.hive_erase.argtypes = [vp, vp, u64, vp, vp]
+        L.hive_execute.argtypes = [vp, vp, vp, vp, u64, vp, vp, vp]
+        L.hive_size.argtypes = [vp, C.POINTER(u64), vp]
+        L.hive_capacity.argtypes = [vp, C.POINTER(u64)]
+        L.hive_clear.argtypes = [vp, vp]
+        L.hive_check.argtypes = [vp, vp]
+        L.hive_stats.argtypes = [vp, C.POINTER(Stats), vp]
+        L.hive_dump.argtypes = [vp, C.POINTER(Image), vp]
+        L.hive_profile_enable.argtypes = [vp, i32]
+        L.hive_profile_read.argtypes = [vp, C.POINTER(Profile)]
+        L.hive_last_error.argtypes = []
+        L.hive_last_error.restype = C.c_char_p
+        for name in EXPORTS:
+            if name not in ("hive_config_default", "hive_last_error"):
+                getattr(L, name).restype = i32
+        _lib = L
+        return L
+
+
+def _raise(L, code):
+    if code != HIVE_OK:
+        raise HiveError(code, L.hive_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dptr(t, itemsize: int, n: int, name: str):
+    """Device pointer of a contiguous CUDA tensor with >= n items of itemsize."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.element_size() != itemsize:
+        raise ValueError(f"{name} must have {itemsize}-byte elements")
+    if t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} elements, need {n}")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class HiveTable:
+    """One Hive table on the current CUDA device (see include/hive.h)."""
+
+    def __init__(self, initial_slots: int = 1 << 20, *, max_slots: int | None = None,
+                 resizable: bool = False, max_evictions: int = 16, resize_batch: int = 1024,
+                 stash_permille: int = 10, grow=(9, 10), shrink=(2, 5),
+                 placement: int = PLACE_BALANCED, lock_spin_limit: int | None = None,
+                 stream=None):
+        self._L = load_library()
+        cfg = Config()
+        self._L.hive_config_default(C.byref(cfg))
+        cfg.initial_slots = int(initial_slots)
+        cfg.max_slots = int(max_slots if max_slots is not None else initial_slots)
+        cfg.max_evictions = int(max_evictions)
+        cfg.resize_batch = int(resize_batch)
+        cfg.stash_permille = int(stash_permille)
+        cfg.grow_num, cfg.grow_den = map(int, grow)
+        cfg.shrink_num, cfg.shrink_den = map(int, shrink)
+        cfg.resizable = 1 if resizable else 0
+        cfg.placement = int(placement)
+        if lock_spin_limit is not None:
+            cfg.lock_spin_limit = int(lock_spin_limit)
+        self.config = cfg
+        h = C.c_void_p()
+        _raise(self._L, self._L.hive_create(C.byref(cfg), _stream_ptr(stream), C.byref(h)))
+        self._h = h
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.hive_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- operations -------------------------------------------------------
+    def insert(self, keys, vals, status=True, stream=None):
+        """Insert/Replace.  Returns the per-op status tensor (uint8) or None."""
+        torch = _torch()
+        n = keys.numel()
+        st = None
+        if status is True:
+            st = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        elif status is not None and status is not False:
+            st = status
+        _raise(self._L, self._L.hive_insert(
+            self._h, _dptr(keys, 4, n, "keys"), _dptr(vals, 4, n, "vals"), n,
+            _dptr(st, 1, n, "status"), _stream_ptr(stream)))
+        return st
+
+    def find(self, keys, vals_out=None, found=True, stream=None):
+        """Search.  Returns (values, found-flags or None); values are 0 on a miss."""
+        torch = _torch()
+        n = keys.numel()
+        if vals_out is None:
+            vals_out = torch.empty(n, dtype=keys.dtype, device=keys.device)
+        fo = None
+        if found is True:
+            fo = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        elif found is not None and found is not False:
+            fo = found
+        _raise(self._L, self._L.hive_find(
+            self._h, _dptr(keys, 4, n, "keys"), n, _dptr(vals_out, 4, n, "vals_out"),
+            _dptr(fo, 1, n, "found"), _stream_ptr(stream)))
+        return vals_out, fo
+
+    def erase(self, keys, status=True, stream=None):
+        torch = _torch()
+        n = keys.numel()
+        st = None
+        if status is True:
+            st = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        elif status is not None and status is not False:
+            st = status
+        _raise(self._L, self._L.hive_erase(
+            self._h, _dptr(keys, 4, n, "keys"), n, _dptr(st, 1, n, "status"), _stream_ptr(stream)))
+        return st
+
+    def execute(self, ops, keys, vals=None, stream=None):
+        """Mixed batch.  Returns (values, status)."""
+        torch = _torch()
+        n = keys.numel()
+        vo = torch.empty(n, dtype=keys.dtype, device=keys.device)
+        st = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        _raise(self._L, self._L.hive_execute(
+            self._h, _dptr(ops, 1, n, "ops"), _dptr(keys, 4, n, "keys"),
+            _dptr(vals, 4, n, "vals") if vals is not None else None, n,
+            _dptr(vo, 4, n, "vals_out"), _dptr(st, 1, n, "status"), _stream_ptr(stream)))
+        return vo, st
+
+    # -- state ------------------------------------------------------------
+    def size(self, stream=None) -> int:
+        out = C.c_uint64()
+        _raise(self._L, self._L.hive_size(self._h, C.byref(out), _stream_ptr(stream)))
+        return int(out.value)
+
+    def capacity(self) -> int:
+        out = C.c_uint64()
+        _raise(self._L, self._L.hive_capacity(self._h, C.byref(out)))
+        return int(out.value)
+
+    def clear(self, stream=None):
+        _raise(self._L, self._L.hive_clear(self._h, _stream_ptr(stream)))
+
+    def check(self, stream=None) -> int:
+        """Sticky device error (0 = none); clears it."""
+        return int(self._L.hive_check(self._h, _stream_ptr(stream)))
+
+    def stats(self, stream=None) -> dict:
+        s = Stats()
+        _raise(self._L, self._L.hive_stats(self._h, C.byref(s), _stream_ptr(stream)))
+        return {f: int(getattr(s, f)) for f, _ in Stats._fields_}
+
+    def profile(self, enable: bool):
+        """Turn per-kernel event timing on or off (see hive_profile_enable)."""
+        _raise(self._L, self._L.hive_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{kind: (ms, launches)} for kernels timed since the last read."""
+        p = Profile()
+        _raise(self._L, self._L.hive_profile_read(self._h, C.byref(p)))
+        return {k: (float(p.ms[i]), int(p.launches[i])) for i, k in enumerate(KERNEL_KINDS)
+                if p.launches[i]}
+
+    def dump(self, stream=None) -> dict:
+        """Host image of the table (numpy arrays) for checks and checkpoints."""
+        img = Image()
+        _raise(self._L, self._L.hive_dump(self._h, C.byref(img), _stream_ptr(stream)))
+        nb, S = int(img.nb), int(img.S)
+        b = np.empty(nb * S, np.uint64)
+        m = np.empty(nb, np.uint32)
+        lk = np.empty(nb, np.uint32)
+        st = np.empty(max(int(img.stash_n), 1), np.uint64)
+        img.buckets = b.ctypes.data
+        img.masks = m.ctypes.data
+        img.locks = lk.ctypes.data
+        img.stash = st.ctypes.data
+        _raise(self._L, self._L.hive_dump(self._h, C.byref(img), _stream_ptr(stream)))
+        return {"nb": nb, "S": S, "M": int(img.M), "p": int(img.p), "buckets": b, "masks": m,
+                "locks": lk, "stash": st[: int(img.stash_n)], "stash_cap": int(img.stash_cap),
+                "size": int(img.size), "pending": int(img.pending)}
+
+
+def to_device_u32(a: np.ndarray, device="cuda"):
+    """numpy uint32 -> CUDA tensor holding the same 32-bit words (int32 storage)."""
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).to(device)
+
+
+def to_host_u32(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint32)
