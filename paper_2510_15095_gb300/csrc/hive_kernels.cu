@@ -30,10 +30,12 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kOpsThreads = 256;
+#ifndef HIVE_OPS_MIN_BLOCKS
+#define HIVE_OPS_MIN_BLOCKS 4  // resident 256-thread blocks per SM the bulk kernel is built for
+#endif
 constexpr int kOvfThreads = 256;
 constexpr int kMaintThreads = 1024;
 constexpr unsigned kMaintSmemWords = 8192;  // 64 KB of words sorted in shared memory
-constexpr int kProbeU = 4;                  // load instructions (2 buckets each) in flight
 
 // Per-op status codes (same numbers as include/hive.h).
 enum : uint8_t {
@@ -202,43 +204,42 @@ __device__ __forceinline__ bool stash_find(const View& v, uint32_t stash_n, uint
 struct LaneCounters {
   int size_delta = 0;
   unsigned replaced = 0, claimed = 0, overflowed = 0, stash_lookups = 0;
-  unsigned long long probes = 0;  // warp-uniform: buckets probed by this warp
+  unsigned probes = 0;  // warp-uniform: buckets probed by this warp
   bool reserved = false, contract = false;
 };
 
-// One probe round: for every op whose bit is set in `need`, read bucket `myb`
-// of that op (the value held by the op's home lane) and match-and-elect.
-// Results land in the home lane: done/status/value, or for inserts the free
-// count and first free slot of the bucket.
+// One probe round over the 32 ops of a warp.  `need` has bit j set when op j
+// (held by lane j, its home lane) must read bucket `myb` this round.  The ops
+// go in four groups of eight; in a group, load u (u = 0..3) of the 16-lane
+// half h reads the bucket of op 2u + h, 16 bytes (two slots) per lane, so the
+// four loads of a lane cover eight buckets.  Match-and-elect (Section III-F)
+// is a ballot per load: the lowest matching lane of a half is the winner, and
+// one shuffle per load hands the matched value to every home lane, which then
+// reads its own op's outcome out of the warp-uniform ballots.  A home lane
+// that must update the matched slot (erase, replace) does the single CAS
+// itself: the expected word is (value << 32 | key), both of which it now holds.
 template <int MODE>
 __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb, uint32_t key,
                                       uint32_t val, uint32_t op, int lane, bool& done,
                                       uint8_t& st, uint32_t& outv, uint32_t& fcnt,
                                       uint32_t& fslot, LaneCounters& cnt) {
   constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
-  const int half = lane >> 4;
+  const int h = lane >> 4;
   const int hl = lane & 15;
-  while (need) {
-    int oa[kProbeU], ob[kProbeU];
+  const int my_g = lane >> 3, my_j = lane & 7, my_u = my_j >> 1, my_h = my_j & 1;
+#pragma unroll 1
+  for (int g = 0; g < 4; ++g) {
+    const unsigned gneed = (need >> (8 * g)) & 0xFFu;
+    if (!gneed) continue;
+    uint64_t wa[4], wb[4];
+    uint32_t kq[4];
 #pragma unroll
-    for (int u = 0; u < kProbeU; ++u) {
-      oa[u] = need ? __ffs(need) - 1 : -1;
-      need &= need - 1u;
-      ob[u] = need ? __ffs(need) - 1 : -1;
-      need &= need - 1u;
-    }
-    uint64_t wa[kProbeU], wb[kProbeU];
-    uint32_t kq[kProbeU], bq[kProbeU], vq[kProbeU], oq[kProbeU];
-#pragma unroll
-    for (int u = 0; u < kProbeU; ++u) {
-      const int o = half ? ob[u] : oa[u];
-      const int src = o & 31;
-      bq[u] = __shfl_sync(kFull, myb, src);
+    for (int u = 0; u < 4; ++u) {
+      const int src = 8 * g + 2 * u + h;
+      const uint32_t bq = __shfl_sync(kFull, myb, src);
       kq[u] = __shfl_sync(kFull, key, src);
-      vq[u] = kIns ? __shfl_sync(kFull, val, src) : 0u;
-      oq[u] = (MODE == kModeMixed) ? __shfl_sync(kFull, op, src) : 0u;
-      if (o >= 0) {
-        const uint64_t* p = v.buckets + static_cast<uint64_t>(bq[u]) * kSlots + 2 * hl;
+      if ((gneed >> (2 * u + h)) & 1u) {
+        const uint64_t* p = v.buckets + static_cast<uint64_t>(bq) * kSlots + 2 * hl;
         if (MODE == kModeFind)
           ld_frag_ro(p, wa[u], wb[u]);
         else
@@ -248,93 +249,91 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
         wb[u] = kEmptyWord;
       }
     }
+    unsigned my_m = 0, my_mh = 0, my_el = 0, my_eh = 0;
+    uint32_t got = 0;
 #pragma unroll
-    for (int u = 0; u < kProbeU; ++u) {
+    for (int u = 0; u < 4; ++u) {
       const bool lo = key_of(wa[u]) == kq[u];
       const bool hi = key_of(wb[u]) == kq[u];
       const unsigned m = __ballot_sync(kFull, lo || hi);
-      unsigned elo = 0, ehi = 0;
-      if (kIns) {
-        elo = __ballot_sync(kFull, wa[u] == kEmptyWord);
-        ehi = __ballot_sync(kFull, wb[u] == kEmptyWord);
+      const unsigned mh = (MODE != kModeFind) ? __ballot_sync(kFull, hi) : 0u;
+      const unsigned el = kIns ? __ballot_sync(kFull, wa[u] == kEmptyWord) : 0u;
+      const unsigned eh = kIns ? __ballot_sync(kFull, wb[u] == kEmptyWord) : 0u;
+      const uint32_t cv = lo ? val_of(wa[u]) : val_of(wb[u]);
+      const unsigned hm = (m >> (16 * my_h)) & 0xFFFFu;
+      const uint32_t x = __shfl_sync(kFull, cv, 16 * my_h + (hm ? __ffs(hm) - 1 : 0));
+      if (u == my_u) {
+        my_m = m;
+        my_mh = mh;
+        my_el = el;
+        my_eh = eh;
+        got = x;
       }
-      // The elected lane's result: the value for a find, CAS success otherwise.
-      uint32_t res = lo ? val_of(wa[u]) : val_of(wb[u]);
-      if (MODE != kModeFind && (lo || hi)) {
-        const int my_o = half ? ob[u] : oa[u];
-        const unsigned hm_mine = (m >> (16 * half)) & 0xFFFFu;
-        if (my_o >= 0 && hl == __ffs(hm_mine) - 1) {
-          const uint32_t opk =
-              MODE == kModeMixed ? oq[u] : (MODE == kModeErase ? OP_ERASE : OP_INSERT);
-          const uint32_t slot = 2 * hl + (lo ? 0 : 1);
-          uint64_t* sp = v.buckets + static_cast<uint64_t>(bq[u]) * kSlots + slot;
-          const uint64_t cur = lo ? wa[u] : wb[u];
+    }
+    if (my_g == g && ((gneed >> my_j) & 1u)) {
+      const unsigned hm = (my_m >> (16 * my_h)) & 0xFFFFu;
+      if (hm) {
+        done = true;
+        const uint32_t opk = MODE == kModeMixed
+                                 ? op
+                                 : (MODE == kModeFind ? OP_FIND
+                                                      : (MODE == kModeErase ? OP_ERASE : OP_INSERT));
+        if (opk == OP_FIND) {
+          outv = got;
+          st = ST_FOUND;
+        } else {
+          const uint32_t w = __ffs(hm) - 1;
+          const uint32_t slot = 2 * w + ((my_mh >> (16 * my_h + w)) & 1u);
+          uint64_t* sp = v.buckets + static_cast<uint64_t>(myb) * kSlots + slot;
+          const uint64_t cur = pack(key, got);
           if (opk == OP_ERASE) {
             // Algorithm 4: CAS the slot to EMPTY, then publish the free bit.
-            res = atomicCAS(ull(sp), cur, kEmptyWord) == cur;
-            if (res) {
-              __threadfence();
-              atomicOr(v.masks + bq[u], 1u << slot);
-            }
-          } else if (opk == OP_INSERT) {
-            // Algorithm 1: CAS the cached word to the new pair.
-            res = atomicCAS(ull(sp), cur, pack(kq[u], vq[u])) == cur;
-          }
-        }
-      }
-#pragma unroll
-      for (int hf = 0; hf < 2; ++hf) {
-        const int o = hf ? ob[u] : oa[u];
-        if (o < 0) continue;
-        const unsigned hm = (m >> (16 * hf)) & 0xFFFFu;
-        if (hm) {
-          const int w = 16 * hf + __ffs(hm) - 1;
-          const uint32_t r = __shfl_sync(kFull, res, w);
-          if (lane == o) {
-            done = true;
-            const uint32_t opk =
-                MODE == kModeMixed ? op : (MODE == kModeFind ? OP_FIND : (MODE == kModeErase ? OP_ERASE : OP_INSERT));
-            if (opk == OP_FIND) {
-              outv = r;
-              st = ST_FOUND;
-            } else if (opk == OP_ERASE) {
-              st = ST_ERASED;
-              if (r) cnt.size_delta -= 1; else cnt.contract = true;
+            // The atomicOr issues only after the CAS has returned, so a
+            // claimer that sees the bit finds the slot already EMPTY.
+            st = ST_ERASED;
+            if (atomicCAS(ull(sp), cur, kEmptyWord) == cur) {
+              atomicOr(v.masks + myb, 1u << slot);
+              cnt.size_delta -= 1;
             } else {
-              st = ST_REPLACED;
-              if (r) cnt.replaced += 1; else cnt.contract = true;
+              cnt.contract = true;
             }
-          }
-        } else if (kIns) {
-          const unsigned ev = (elo >> (16 * hf)) & 0xFFFFu;
-          const unsigned od = (ehi >> (16 * hf)) & 0xFFFFu;
-          if (lane == o) {
-            fcnt = __popc(ev) + __popc(od);
-            const uint32_t se = ev ? 2u * (__ffs(ev) - 1) : kSlots;
-            const uint32_t so = od ? 2u * (__ffs(od) - 1) + 1u : kSlots;
-            fslot = se < so ? se : so;
+          } else {
+            // Algorithm 1: CAS the cached word to the new pair.
+            st = ST_REPLACED;
+            if (atomicCAS(ull(sp), cur, pack(key, val)) == cur)
+              cnt.replaced += 1;
+            else
+              cnt.contract = true;
           }
         }
+      } else if (kIns) {
+        const unsigned ev = (my_el >> (16 * my_h)) & 0xFFFFu;
+        const unsigned od = (my_eh >> (16 * my_h)) & 0xFFFFu;
+        fcnt = __popc(ev) + __popc(od);
+        const uint32_t se = ev ? 2u * (__ffs(ev) - 1) : kSlots;
+        const uint32_t so = od ? 2u * (__ffs(od) - 1) + 1u : kSlots;
+        fslot = se < so ? se : so;
       }
     }
   }
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kOpsThreads)
+__global__ void __launch_bounds__(kOpsThreads, HIVE_OPS_MIN_BLOCKS)
     k_ops(View v, const uint8_t* __restrict__ ops, const uint32_t* __restrict__ keys,
           const uint32_t* __restrict__ vals, uint64_t n, uint32_t* __restrict__ vals_out,
           uint8_t* __restrict__ found, uint8_t* __restrict__ status, List ovf) {
   constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
   const int lane = threadIdx.x & 31;
-  const uint64_t warp0 = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
-  const uint64_t nchunks = (n + 31) >> 5;
+  // n < 2^32 per call, so chunk and op indices fit 32 bits
+  const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t nchunks = static_cast<uint32_t>((n + 31) >> 5);
   const uint32_t stash_n = v.ctrl->stash_n;
   LaneCounters cnt;
 
-  for (uint64_t c = warp0; c < nchunks; c += nwarps) {
-    const uint64_t i = (c << 5) + lane;
+  for (uint32_t c = warp0; c < nchunks; c += nwarps) {
+    const uint32_t i = (c << 5) + lane;
     const bool valid = i < n;
     uint32_t op = OP_FIND;
     if (MODE == kModeMixed)
@@ -429,7 +428,7 @@ __global__ void __launch_bounds__(kOpsThreads)
         if (to_ovf) {
           const unsigned r = base + __popc(om & ((1u << lane) - 1u));
           ovf.words[r] = pack(key, val);
-          ovf.idx[r] = static_cast<uint32_t>(i);
+          ovf.idx[r] = i;
         }
       }
     }
@@ -454,7 +453,8 @@ __global__ void __launch_bounds__(kOpsThreads)
   const unsigned ct = __ballot_sync(kFull, cnt.contract);
   const unsigned sl = __reduce_add_sync(kFull, cnt.stash_lookups);
   if (lane == 0) {
-    if (cnt.probes) atomicAdd(&v.ctrl->stats[kStProbes], cnt.probes);
+    if (cnt.probes)
+      atomicAdd(&v.ctrl->stats[kStProbes], static_cast<unsigned long long>(cnt.probes));
     if (sl) atomicAdd(&v.ctrl->stats[kStStashLookups], static_cast<unsigned long long>(sl));
     if (sd) atomicAdd(&v.ctrl->size, static_cast<unsigned long long>(static_cast<long long>(sd)));
     if (rp) atomicAdd(&v.ctrl->stats[kStReplaced], static_cast<unsigned long long>(rp));
