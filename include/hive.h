@@ -223,6 +223,24 @@ hive_status hive_profile_enable(hive_table* t, int enable);
  * and forgets them.  Synchronises on the recorded events. */
 hive_status hive_profile_read(hive_table* t, hive_profile_t* out);
 
+/* Insert into a FIXED-capacity table without allocating anything.  The paper
+ * has no counterpart; this is a library convenience.  Same inputs, outputs and
+ * results as hive_insert, for callers that must not call cudaMalloc: a process
+ * whose device memory is all pre-reserved by another allocator, or a
+ * latency-bound loop that cannot stall behind the device synchronisation that
+ * precedes hive_insert's on-demand growth of its scratch list.  The list of
+ * inserts handed to the eviction kernel lives instead in one file-scope device
+ * array of 2^18 entries (3 MiB per GPU, held until exit).
+ *  - n must be <= 2^18 (262,144) per call, else HIVE_ERR_INVALID_ARG and nothing
+ *    is queued; a resizable table also gives HIVE_ERR_INVALID_ARG.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the array: calls whose work overlaps on the GPU (e.g. on
+ *    two streams at once) race and must not be issued. */
+hive_status hive_insert_noalloc(hive_table* t, const uint32_t* keys, const uint32_t* vals,
+                                uint64_t n, uint8_t* status, void* stream);
+
 /* Text of the calling thread's last error (never NULL). */
 const char* hive_last_error(void);
 

@@ -321,6 +321,17 @@ hive_status check_n(uint64_t n) {
 
 }  // namespace
 
+namespace hive {
+bool table_view(const hive_table* t, View* v, Launch* L, bool* resizable) {
+  if (!t) return false;
+  *v = make_view(t);
+  *L = t->L;
+  *resizable = t->cfg.resizable != 0;
+  return true;
+}
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace hive
+
 extern "C" {
 
 void hive_config_default(hive_config* cfg) {

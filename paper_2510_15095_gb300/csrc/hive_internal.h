@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace hive {
 
 constexpr uint32_t kSlots = 32;                    // S, slots per bucket (Section III-A)
@@ -104,4 +106,12 @@ cudaError_t launch_count_inserts(const uint8_t* ops, uint64_t n, unsigned int* o
                                  cudaStream_t s);
 cudaError_t query_occupancy(Launch* L);
 
+}  // namespace hive
+
+// Read-only access to a table's device view for other translation units of
+// the library (hive_host.cpp defines these).
+struct hive_table;
+namespace hive {
+bool table_view(const hive_table* t, View* v, Launch* L, bool* resizable);
+void set_last_error(const std::string& msg);  // text returned by hive_last_error()
 }  // namespace hive

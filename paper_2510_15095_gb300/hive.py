@@ -29,7 +29,7 @@ PLACE_BALANCED, PLACE_FIRST = 0, 1
 EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", "hive_find",
            "hive_erase", "hive_execute", "hive_size", "hive_capacity", "hive_clear", "hive_check",
            "hive_stats", "hive_dump", "hive_profile_enable", "hive_profile_read",
-           "hive_last_error"]
+           "hive_insert_noalloc", "hive_last_error"]
 KERNEL_KINDS = ["find", "insert", "erase", "mixed", "evict", "maint", "split", "merge", "count"]
 
 
@@ -97,6 +97,7 @@ def load_library(path: str = LIB_PATH):
         L.hive_check.argtypes = [vp, vp]
         L.hive_stats.argtypes = [vp, C.POINTER(Stats), vp]
         L.hive_dump.argtypes = [vp, C.POINTER(Image), vp]
+        L.hive_insert_noalloc.argtypes = [vp, vp, vp, u64, vp, vp]
         L.hive_profile_enable.argtypes = [vp, i32]
         L.hive_profile_read.argtypes = [vp, C.POINTER(Profile)]
         L.hive_last_error.argtypes = []
@@ -196,6 +197,21 @@ class HiveTable:
         elif status is not None and status is not False:
             st = status
         _raise(self._L, self._L.hive_insert(
+            self._h, _dptr(keys, 4, n, "keys"), _dptr(vals, 4, n, "vals"), n,
+            _dptr(st, 1, n, "status"), _stream_ptr(stream)))
+        return st
+
+    def insert_noalloc(self, keys, vals, status=True, stream=None):
+        """hive_insert_noalloc: the fixed-table insert that allocates nothing
+        (for callers that must not call cudaMalloc); at most 2^18 ops."""
+        torch = _torch()
+        n = keys.numel()
+        st = None
+        if status is True:
+            st = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        elif status is not None and status is not False:
+            st = status
+        _raise(self._L, self._L.hive_insert_noalloc(
             self._h, _dptr(keys, 4, n, "keys"), _dptr(vals, 4, n, "vals"), n,
             _dptr(st, 1, n, "status"), _stream_ptr(stream)))
         return st
