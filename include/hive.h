@@ -223,6 +223,52 @@ hive_status hive_profile_enable(hive_table* t, int enable);
  * and forgets them.  Synchronises on the recorded events. */
 hive_status hive_profile_read(hive_table* t, hive_profile_t* out);
 
+/* ---- Multi-table batches (many independent tables, one launch per phase) ----
+ * Not in the paper: the tables are the paper's, the batching is a library
+ * layer for services that hold many tables.  A batch is a list of segments;
+ * each segment is a mixed op range (HIVE_OP_* codes, as in hive_execute) on one
+ * table.  Per table, the ops of all its segments in one call obey the batch
+ * contract of hive_execute, and the results equal running those segments
+ * through hive_execute on that table.  Differences from hive_execute:
+ *  - a resizable table grows before the batch for n_insert new keys of its
+ *    segments (give the exact insert count, or n); an insert that still finds
+ *    no room (stash full) reports FULL instead of growing mid-batch;
+ *  - find statuses are FOUND / NOT_FOUND like hive_execute; there is no
+ *    separate found-flag array. */
+typedef struct hive_multi hive_multi;
+
+typedef struct {
+  uint32_t table;         /* index into the tables given to hive_multi_create */
+  uint32_t reserved0;     /* must be 0 */
+  uint64_t n;             /* ops in this segment, < 2^32 */
+  uint64_t n_insert;      /* upper bound of HIVE_OP_INSERT ops among them */
+  const uint8_t* ops;     /* [n] HIVE_OP_* (device) */
+  const uint32_t* keys;   /* [n] (device) */
+  const uint32_t* vals;   /* [n] insert values (device, nullable without inserts) */
+  uint32_t* vals_out;     /* [n] find results, 0 otherwise (device, nullable) */
+  uint8_t* status;        /* [n] per-op status (device, nullable) */
+} hive_segment;
+
+/* Groups tables (created by hive_create on the current device) for batched
+ * calls.  max_segments and max_ops bound one batch; use_graph != 0 captures
+ * the fixed kernel sequence into a CUDA graph on the first call and replays it
+ * afterwards.  The tables stay owned by the caller and must outlive the
+ * group; they may still be used one by one between batches (same stream). */
+hive_status hive_multi_create(hive_table* const* tables, uint32_t n_tables,
+                              uint32_t max_segments, uint64_t max_ops, int use_graph,
+                              void* stream, hive_multi** out);
+
+/* Runs one batch on `stream`.  Consecutive batches of one group go on one
+ * stream.  With only fixed tables the call does not synchronise; with
+ * resizable tables it waits once for the batch (to apply the contraction
+ * policy to all tables).  Errors: INVALID_ARG (bad segment, too many ops,
+ * segments or split launches), CUDA. */
+hive_status hive_multi_execute(hive_multi* m, const hive_segment* segs, uint32_t n_segs,
+                               void* stream);
+
+/* Frees the group (not its tables).  Synchronises the device first. */
+hive_status hive_multi_destroy(hive_multi* m);
+
 /* Insert into a FIXED-capacity table without allocating anything.  The paper
  * has no counterpart; this is a library convenience.  Same inputs, outputs and
  * results as hive_insert, for callers that must not call cudaMalloc: a process

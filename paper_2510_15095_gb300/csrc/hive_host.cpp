@@ -63,38 +63,6 @@ uint64_t next_pow2(uint64_t x) {
 
 }  // namespace
 
-struct hive_table {
-  hive_config cfg;
-  int device = 0;
-  Launch L{};
-  uint64_t nb_init = 0, nb_max = 0, nb = 0;
-  uint32_t M = 0, p = 0;
-  uint32_t stash_cap = 0;
-  uint64_t stash_alloc = 0;
-  uint64_t* buckets = nullptr;
-  uint32_t* masks = nullptr;
-  uint32_t* locks = nullptr;
-  uint64_t* stash_kv = nullptr;
-  uint32_t* stash_keys = nullptr;
-  Ctrl* ctrl = nullptr;
-  Ctrl* host_ctrl = nullptr;  // pinned readback buffer
-  uint64_t list_cap = 0;
-  uint64_t* la_words = nullptr;  // list A: bulk kernel -> eviction kernel
-  uint32_t* la_idx = nullptr;
-  uint64_t* lb_words = nullptr;  // list B: items that found no room
-  uint32_t* lb_idx = nullptr;
-  uint64_t size_host = 0;       // exact after each resizable call
-  uint64_t splits = 0, merges = 0;
-  bool merge_deferred = false;
-  // profiling hook: events bracketing each launch while enabled
-  struct Rec {
-    int kind;
-    cudaEvent_t a, b;
-  };
-  bool prof = false;
-  std::vector<Rec> recs;
-  std::vector<cudaEvent_t> ev_pool;
-};
 
 namespace {
 
@@ -126,7 +94,9 @@ cudaEvent_t ev_get(hive_table* t) {
     }                                                                       \
   } while (0)
 
-View make_view(const hive_table* t) {
+}  // namespace
+
+View hive::make_view(const hive_table* t) {
   View v{};
   v.buckets = t->buckets;
   v.masks = t->masks;
@@ -143,6 +113,8 @@ View make_view(const hive_table* t) {
   v.placement = t->cfg.placement;
   return v;
 }
+
+namespace {
 
 List list_a(const hive_table* t) { return List{t->la_words, t->la_idx, &t->ctrl->ovf_n}; }
 List list_b(const hive_table* t) { return List{t->lb_words, t->lb_idx, &t->ctrl->pend_n}; }
@@ -183,38 +155,15 @@ hive_status readback(hive_table* t, cudaStream_t s) {
   return HIVE_OK;
 }
 
-bool over_grow(const hive_table* t, uint64_t live, uint64_t nb) {
-  return static_cast<unsigned __int128>(live) * t->cfg.grow_den >
-         static_cast<unsigned __int128>(kSlots) * nb * t->cfg.grow_num;
-}
-bool under_shrink(const hive_table* t, uint64_t live, uint64_t nb) {
-  return static_cast<unsigned __int128>(live) * t->cfg.shrink_den <
-         static_cast<unsigned __int128>(kSlots) * nb * t->cfg.shrink_num;
-}
-
 // One expansion launch (Section IV-C1).
 hive_status split_step(hive_table* t, cudaStream_t s, bool* did) {
-  *did = false;
-  const uint64_t room = static_cast<uint64_t>(t->M) + 1 - t->p;
-  const uint64_t step = std::min<uint64_t>({t->cfg.resize_batch, room, t->nb_max - t->nb});
-  if (step == 0) return HIVE_OK;
-  const uint32_t src0 = t->p, half = t->M + 1u;
-  t->p += static_cast<uint32_t>(step);
-  t->nb += step;
-  if (t->p == t->M + 1u) {
-    t->M = 2u * t->M + 1u;
-    t->p = 0;
-  }
-  HIVE_LAUNCH(t, HIVE_K_SPLIT, s, launch_split(make_view(t), src0, static_cast<uint32_t>(step), half, s));
-  t->splits += step;
-  *did = true;
-  return HIVE_OK;
-}
-
-// After a resize the stash may have words that now fit a bucket; make the
-// next maintenance pass look at it.
-hive_status mark_stash_dirty(hive_table* t, cudaStream_t s) {
-  HIVE_CK(cudaMemsetAsync(&t->ctrl->stash_dirty, 1, 1, s));
+  SplitPlan pl{};
+  *did = plan_split(t, &pl);
+  if (!*did) return HIVE_OK;
+  View v = make_view(t);
+  v.M = pl.M;
+  v.p = pl.p;
+  HIVE_LAUNCH(t, HIVE_K_SPLIT, s, launch_split(v, pl.src0, pl.count, pl.half, s));
   return HIVE_OK;
 }
 
@@ -266,6 +215,30 @@ hive_status finish_resizable(hive_table* t, uint8_t* status, cudaStream_t s) {
   if (st != HIVE_OK) return st;
   t->size_host = t->host_ctrl->size;
 
+  return contract_table(t, s);
+}
+
+}  // namespace
+
+bool hive::over_grow(const hive_table* t, uint64_t live, uint64_t nb) {
+  return static_cast<unsigned __int128>(live) * t->cfg.grow_den >
+         static_cast<unsigned __int128>(kSlots) * nb * t->cfg.grow_num;
+}
+bool hive::under_shrink(const hive_table* t, uint64_t live, uint64_t nb) {
+  return static_cast<unsigned __int128>(live) * t->cfg.shrink_den <
+         static_cast<unsigned __int128>(kSlots) * nb * t->cfg.shrink_num;
+}
+
+
+// After a resize the stash may have words that now fit a bucket; make the
+// next maintenance pass look at it.
+hive_status hive::mark_stash_dirty(hive_table* t, cudaStream_t s) {
+  HIVE_CK(cudaMemsetAsync(&t->ctrl->stash_dirty, 1, 1, s));
+  return HIVE_OK;
+}
+
+hive_status hive::contract_table(hive_table* t, cudaStream_t s) {
+  hive_status st = HIVE_OK;
   // Contraction (Section IV-C2).
   t->merge_deferred = false;
   while (t->nb > t->nb_init && under_shrink(t, t->size_host, t->nb)) {
@@ -308,6 +281,27 @@ hive_status finish_resizable(hive_table* t, uint8_t* status, cudaStream_t s) {
   }
   return HIVE_OK;
 }
+
+bool hive::plan_split(hive_table* t, SplitPlan* out) {
+  const uint64_t room = static_cast<uint64_t>(t->M) + 1 - t->p;
+  const uint64_t step = std::min<uint64_t>({t->cfg.resize_batch, room, t->nb_max - t->nb});
+  if (step == 0) return false;
+  out->src0 = t->p;
+  out->half = t->M + 1u;
+  out->count = static_cast<uint32_t>(step);
+  t->p += static_cast<uint32_t>(step);
+  t->nb += step;
+  if (t->p == t->M + 1u) {
+    t->M = 2u * t->M + 1u;
+    t->p = 0;
+  }
+  out->M = t->M;
+  out->p = t->p;
+  t->splits += step;
+  return true;
+}
+
+namespace {
 
 hive_status check_table(hive_table* t) {
   if (!t) return fail(HIVE_ERR_INVALID_ARG, "table is NULL");

@@ -6,6 +6,9 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
+
+#include "hive.h"
 
 namespace hive {
 
@@ -81,6 +84,33 @@ struct List {
   uint64_t* words;
   uint32_t* idx;   // caller op index or kNoOp
   unsigned int* count;
+  uint32_t* seg;   // multi-table batches: segment of each entry (else NULL)
+};
+
+// One (table, op range) of a multi-table batch; 64 bytes.
+struct MultiSeg {
+  uint32_t table;        // index into the batch's view array
+  uint32_t n;            // ops
+  uint32_t chunk0;       // first 32-op chunk of this segment within the batch
+  uint32_t pad;
+  const uint8_t* ops;    // HIVE_OP_* per op
+  const uint32_t* keys;
+  const uint32_t* vals;  // insert values (nullable)
+  uint32_t* vals_out;    // find results (nullable)
+  uint8_t* status;       // per-op status (nullable)
+  uint64_t pad2;
+};
+
+// One split launch of one table inside a wave of a multi-table batch.
+struct MultiJob {
+  uint32_t table, src0, count, half;
+  uint32_t pair0;  // first warp of this job within the wave
+  uint32_t M, p;   // the table's linear-hashing state after this job
+  uint32_t pad;
+};
+
+struct MultiHdr {
+  uint32_t n_segs, total_chunks, n_tables, pad;
 };
 
 enum OpMode : int { kModeFind = 0, kModeInsert = 1, kModeErase = 2, kModeMixed = 3 };
@@ -89,6 +119,7 @@ struct Launch {
   int num_sms;
   int ops_blocks_per_sm;
   int ovf_blocks_per_sm;
+  int multi_blocks_per_sm;
 };
 
 // Kernel launchers (hive_kernels.cu).  Each returns the launch error.
@@ -104,14 +135,70 @@ cudaError_t launch_merge_excess(const View& v_new, uint32_t count, cudaStream_t 
 cudaError_t launch_merge(const View& v_new, uint32_t count, List ovf, cudaStream_t s);
 cudaError_t launch_count_inserts(const uint8_t* ops, uint64_t n, unsigned int* out,
                                  cudaStream_t s);
+cudaError_t launch_multi_ops(const MultiHdr* hdr, const MultiSeg* segs, const View* views, List ovf,
+                             const Launch& L, cudaStream_t s);
+cudaError_t launch_multi_overflow(const MultiSeg* segs, const View* views, List in,
+                                  const Launch& L, cudaStream_t s);
+cudaError_t launch_multi_maint(const View* views, uint32_t n_tables, cudaStream_t s);
+cudaError_t launch_multi_split(const MultiJob* jobs, uint32_t n_jobs, uint32_t total_pairs,
+                               const View* views, cudaStream_t s);
+cudaError_t launch_multi_gather(const View* views, uint32_t n_tables, unsigned long long* out,
+                                cudaStream_t s);
 cudaError_t query_occupancy(Launch* L);
 
 }  // namespace hive
 
-// Read-only access to a table's device view for other translation units of
-// the library (hive_host.cpp defines these).
-struct hive_table;
+// The table object behind the opaque handle of include/hive.h.
+struct hive_table {
+  hive_config cfg;
+  int device = 0;
+  hive::Launch L{};
+  uint64_t nb_init = 0, nb_max = 0, nb = 0;
+  uint32_t M = 0, p = 0;
+  uint32_t stash_cap = 0;
+  uint64_t stash_alloc = 0;
+  uint64_t* buckets = nullptr;
+  uint32_t* masks = nullptr;
+  uint32_t* locks = nullptr;
+  uint64_t* stash_kv = nullptr;
+  uint32_t* stash_keys = nullptr;
+  hive::Ctrl* ctrl = nullptr;
+  hive::Ctrl* host_ctrl = nullptr;  // pinned readback buffer
+  uint64_t list_cap = 0;
+  uint64_t* la_words = nullptr;  // list A: bulk kernel -> eviction kernel
+  uint32_t* la_idx = nullptr;
+  uint64_t* lb_words = nullptr;  // list B: items that found no room
+  uint32_t* lb_idx = nullptr;
+  uint64_t size_host = 0;       // exact after each resizable call
+  uint64_t splits = 0, merges = 0;
+  bool merge_deferred = false;
+  // profiling hook: events bracketing each launch while enabled
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool prof = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> ev_pool;
+};
+
+// Helpers shared by the translation units of the library (hive_host.cpp
+// defines these).
 namespace hive {
+View make_view(const hive_table* t);
+// The next expansion launch of a table (Section IV-C1): bucket pairs
+// (src0 + i, src0 + i + half) for i < count, leaving the table at (M, p).
+struct SplitPlan {
+  uint32_t src0, count, half, M, p;
+};
+// Advances the host-side state of t by one split launch and returns its plan;
+// false when the table is at nb_max.
+bool plan_split(hive_table* t, SplitPlan* out);
+bool over_grow(const hive_table* t, uint64_t live, uint64_t nb);
+bool under_shrink(const hive_table* t, uint64_t live, uint64_t nb);
+// Contraction loop after a batch (Section IV-C2); reads counters back.
+hive_status contract_table(hive_table* t, cudaStream_t s);
+hive_status mark_stash_dirty(hive_table* t, cudaStream_t s);
 bool table_view(const hive_table* t, View* v, Launch* L, bool* resizable);
 void set_last_error(const std::string& msg);  // text returned by hive_last_error()
 }  // namespace hive

@@ -30,6 +30,9 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kOpsThreads = 256;
+#ifndef HIVE_MULTI_MIN_BLOCKS
+#define HIVE_MULTI_MIN_BLOCKS 3  // the multi-table bulk kernel also holds a table view per warp
+#endif
 #ifndef HIVE_OPS_MIN_BLOCKS
 #define HIVE_OPS_MIN_BLOCKS 4  // resident 256-thread blocks per SM the bulk kernel is built for
 #endif
@@ -318,133 +321,19 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
   }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kOpsThreads, HIVE_OPS_MIN_BLOCKS)
-    k_ops(View v, const uint8_t* __restrict__ ops, const uint32_t* __restrict__ keys,
-          const uint32_t* __restrict__ vals, uint64_t n, uint32_t* __restrict__ vals_out,
-          uint8_t* __restrict__ found, uint8_t* __restrict__ status, List ovf) {
-  constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
-  const int lane = threadIdx.x & 31;
-  // n < 2^32 per call, so chunk and op indices fit 32 bits
-  const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t nchunks = static_cast<uint32_t>((n + 31) >> 5);
-  const uint32_t stash_n = v.ctrl->stash_n;
-  LaneCounters cnt;
+// Op arrays of one batch, or of one segment of a multi-table batch.
+struct OpPtrs {
+  const uint8_t* ops;
+  const uint32_t* keys;
+  const uint32_t* vals;
+  uint32_t* vals_out;
+  uint8_t* found;
+  uint8_t* status;
+};
 
-  for (uint32_t c = warp0; c < nchunks; c += nwarps) {
-    const uint32_t i = (c << 5) + lane;
-    const bool valid = i < n;
-    uint32_t op = OP_FIND;
-    if (MODE == kModeMixed)
-      op = valid ? static_cast<uint32_t>(__ldcs(ops + i)) : OP_FIND;
-    else if (MODE == kModeInsert)
-      op = OP_INSERT;
-    else if (MODE == kModeErase)
-      op = OP_ERASE;
-    if (op > OP_ERASE) op = OP_FIND;  // unknown op codes read only
-    const uint32_t key = valid ? __ldcs(keys + i) : kEmptyKey;
-    uint32_t val = 0;
-    if (kIns && valid && op == OP_INSERT && vals) val = __ldcs(vals + i);
-    const bool reserved = valid && key >= kReservedKeyMin;
-    const bool live = valid && !reserved;
-    cnt.reserved |= reserved;
-
-    const uint32_t b1 = lh_bucket(bithash1(key), v.M, v.p);
-    const uint32_t b2 = lh_bucket(bithash2(key), v.M, v.p);
-    bool done = !live;
-    uint8_t st = reserved ? ST_RESERVED : ST_NOT_FOUND;
-    uint32_t outv = 0;
-    uint32_t f1 = 0, s1 = kSlots, f2 = 0, s2 = kSlots;
-
-    // Probe the BitHash1 bucket of every op, then the BitHash2 bucket of the
-    // ops still unresolved (Section IV-B: WCME over the d = 2 candidates).
-    unsigned need = __ballot_sync(kFull, !done);
-    cnt.probes += __popc(need);
-    if (need) probe<MODE>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt);
-    need = __ballot_sync(kFull, !done);
-    cnt.probes += __popc(need);
-    if (need) probe<MODE>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt);
-
-    // The stash (Section IV-A step 4) holds keys that found no bucket room.
-    if (!done && stash_n) {
-      uint32_t pos;
-      cnt.stash_lookups += 1;
-      if (stash_find(v, stash_n, key, pos)) {
-        uint64_t* sp = v.stash_kv + pos;
-        const uint64_t w = ld_relaxed64(sp);
-        if (key_of(w) == key) {
-          done = true;
-          if (op == OP_FIND) {
-            outv = val_of(w);
-            st = ST_FOUND;
-          } else if (op == OP_ERASE) {
-            st = ST_ERASED;
-            if (atomicCAS(ull(sp), w, kEmptyWord) == w) {
-              cnt.size_delta -= 1;
-              atomicExch(&v.ctrl->stash_dirty, 1u);
-            } else {
-              cnt.contract = true;
-            }
-          } else {
-            st = ST_REPLACED;
-            if (atomicCAS(ull(sp), w, pack(key, val)) == w) cnt.replaced += 1; else cnt.contract = true;
-          }
-        }
-      }
-    }
-
-    // Step 2: claim-then-commit for absent keys.
-    bool to_ovf = false;
-    if (kIns && !done && op == OP_INSERT) {
-      const uint64_t word = pack(key, val);
-      const bool first1 = v.placement ? (f1 > 0) : (f1 >= f2);
-      const uint32_t tb = first1 ? b1 : b2, ts = first1 ? s1 : s2;
-      const uint32_t ob = first1 ? b2 : b1, os = first1 ? s2 : s1;
-      bool placed = false;
-      if (f1 + f2 > 0) {
-        placed = claim_store(v, tb, ts, word);
-        if (!placed && ob != tb) placed = claim_store(v, ob, os, word);
-      }
-      if (placed) {
-        done = true;
-        st = ST_INSERTED;
-        cnt.size_delta += 1;
-        cnt.claimed += 1;
-      } else {
-        to_ovf = true;
-        cnt.overflowed += 1;
-      }
-    }
-
-    // Hand full-bucket inserts to the eviction kernel (steps 3-4).
-    if (kIns) {
-      const unsigned om = __ballot_sync(kFull, to_ovf);
-      if (om) {
-        const int leader = __ffs(om) - 1;
-        unsigned base = 0;
-        if (lane == leader) base = atomicAdd(ovf.count, static_cast<unsigned>(__popc(om)));
-        base = __shfl_sync(kFull, base, leader);
-        if (to_ovf) {
-          const unsigned r = base + __popc(om & ((1u << lane) - 1u));
-          ovf.words[r] = pack(key, val);
-          ovf.idx[r] = i;
-        }
-      }
-    }
-
-    if (valid) {
-      if (MODE == kModeFind) {
-        __stcs(vals_out + i, outv);
-        if (found) found[i] = st == ST_FOUND ? 1 : 0;
-      } else {
-        if (status && !to_ovf) status[i] = st;
-        if (MODE == kModeMixed && vals_out) __stcs(vals_out + i, outv);
-      }
-    }
-  }
-
-  // One atomic per warp per counter.
+// Adds a warp's counters to the table of `v` and clears them: one atomic per
+// non-zero counter.
+__device__ __forceinline__ void flush_counters(const View& v, LaneCounters& cnt, int lane) {
   const int sd = __reduce_add_sync(kFull, static_cast<unsigned>(cnt.size_delta));
   const unsigned rp = __reduce_add_sync(kFull, cnt.replaced);
   const unsigned cl = __reduce_add_sync(kFull, cnt.claimed);
@@ -463,6 +352,141 @@ __global__ void __launch_bounds__(kOpsThreads, HIVE_OPS_MIN_BLOCKS)
     if (rs) atomicOr(&v.ctrl->err, kErrReserved);
     if (ct) atomicOr(&v.ctrl->err, kErrContract);
   }
+  cnt = LaneCounters();
+}
+
+// Ops [32c, 32c + 32) of a batch of n ops on the table of `v`.  Full-bucket
+// inserts go to the overflow list, tagged with `seg` when the list keeps tags.
+template <int MODE>
+__device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const OpPtrs a,
+                                          uint32_t c, uint64_t n, const List ovf, uint32_t seg,
+                                          LaneCounters& cnt, int lane) {
+  constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
+  const uint32_t i = (c << 5) + lane;
+  const bool valid = i < n;
+  uint32_t op = OP_FIND;
+  if (MODE == kModeMixed)
+    op = valid ? static_cast<uint32_t>(__ldcs(a.ops + i)) : OP_FIND;
+  else if (MODE == kModeInsert)
+    op = OP_INSERT;
+  else if (MODE == kModeErase)
+    op = OP_ERASE;
+  if (op > OP_ERASE) op = OP_FIND;  // unknown op codes read only
+  const uint32_t key = valid ? __ldcs(a.keys + i) : kEmptyKey;
+  uint32_t val = 0;
+  if (kIns && valid && op == OP_INSERT && a.vals) val = __ldcs(a.vals + i);
+  const bool reserved = valid && key >= kReservedKeyMin;
+  const bool live = valid && !reserved;
+  cnt.reserved |= reserved;
+
+  const uint32_t b1 = lh_bucket(bithash1(key), v.M, v.p);
+  const uint32_t b2 = lh_bucket(bithash2(key), v.M, v.p);
+  bool done = !live;
+  uint8_t st = reserved ? ST_RESERVED : ST_NOT_FOUND;
+  uint32_t outv = 0;
+  uint32_t f1 = 0, s1 = kSlots, f2 = 0, s2 = kSlots;
+
+  // Probe the BitHash1 bucket of every op, then the BitHash2 bucket of the
+  // ops still unresolved (Section IV-B: WCME over the d = 2 candidates).
+  unsigned need = __ballot_sync(kFull, !done);
+  cnt.probes += __popc(need);
+  if (need) probe<MODE>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt);
+  need = __ballot_sync(kFull, !done);
+  cnt.probes += __popc(need);
+  if (need) probe<MODE>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt);
+
+  // The stash (Section IV-A step 4) holds keys that found no bucket room.
+  if (!done && stash_n) {
+    uint32_t pos;
+    cnt.stash_lookups += 1;
+    if (stash_find(v, stash_n, key, pos)) {
+      uint64_t* sp = v.stash_kv + pos;
+      const uint64_t w = ld_relaxed64(sp);
+      if (key_of(w) == key) {
+        done = true;
+        if (op == OP_FIND) {
+          outv = val_of(w);
+          st = ST_FOUND;
+        } else if (op == OP_ERASE) {
+          st = ST_ERASED;
+          if (atomicCAS(ull(sp), w, kEmptyWord) == w) {
+            cnt.size_delta -= 1;
+            atomicExch(&v.ctrl->stash_dirty, 1u);
+          } else {
+            cnt.contract = true;
+          }
+        } else {
+          st = ST_REPLACED;
+          if (atomicCAS(ull(sp), w, pack(key, val)) == w) cnt.replaced += 1; else cnt.contract = true;
+        }
+      }
+    }
+  }
+
+  // Step 2: claim-then-commit for absent keys.
+  bool to_ovf = false;
+  if (kIns && !done && op == OP_INSERT) {
+    const uint64_t word = pack(key, val);
+    const bool first1 = v.placement ? (f1 > 0) : (f1 >= f2);
+    const uint32_t tb = first1 ? b1 : b2, ts = first1 ? s1 : s2;
+    const uint32_t ob = first1 ? b2 : b1, os = first1 ? s2 : s1;
+    bool placed = false;
+    if (f1 + f2 > 0) {
+      placed = claim_store(v, tb, ts, word);
+      if (!placed && ob != tb) placed = claim_store(v, ob, os, word);
+    }
+    if (placed) {
+      done = true;
+      st = ST_INSERTED;
+      cnt.size_delta += 1;
+      cnt.claimed += 1;
+    } else {
+      to_ovf = true;
+      cnt.overflowed += 1;
+    }
+  }
+
+  // Hand full-bucket inserts to the eviction kernel (steps 3-4).
+  if (kIns) {
+    const unsigned om = __ballot_sync(kFull, to_ovf);
+    if (om) {
+      const int leader = __ffs(om) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(ovf.count, static_cast<unsigned>(__popc(om)));
+      base = __shfl_sync(kFull, base, leader);
+      if (to_ovf) {
+        const unsigned r = base + __popc(om & ((1u << lane) - 1u));
+        ovf.words[r] = pack(key, val);
+        ovf.idx[r] = i;
+        if (ovf.seg) ovf.seg[r] = seg;
+      }
+    }
+  }
+
+  if (valid) {
+    if (MODE == kModeFind) {
+      __stcs(a.vals_out + i, outv);
+      if (a.found) a.found[i] = st == ST_FOUND ? 1 : 0;
+    } else {
+      if (a.status && !to_ovf) a.status[i] = st;
+      if (MODE == kModeMixed && a.vals_out) __stcs(a.vals_out + i, outv);
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kOpsThreads, HIVE_OPS_MIN_BLOCKS)
+    k_ops(View v, OpPtrs a, uint64_t n, List ovf) {
+  const int lane = threadIdx.x & 31;
+  // n < 2^32 per call, so chunk and op indices fit 32 bits
+  const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t nchunks = static_cast<uint32_t>((n + 31) >> 5);
+  const uint32_t stash_n = v.ctrl->stash_n;
+  LaneCounters cnt;
+  for (uint32_t c = warp0; c < nchunks; c += nwarps)
+    run_chunk<MODE>(v, stash_n, a, c, n, ovf, 0, cnt, lane);
+  flush_counters(v, cnt, lane);
 }
 
 // ----------------------------------------------------------------------------
@@ -486,135 +510,151 @@ __device__ __forceinline__ bool stash_reserve(const View& v) {
   return false;
 }
 
+// Counters of the eviction kernel, kept by lane 0 of a warp.
+struct OvfCounters {
+  unsigned claim = 0, rounds = 0, locks = 0, to = 0, stash = 0, pend = 0, added = 0;
+};
+
+__device__ __forceinline__ void flush_ovf_counters(const View& v, OvfCounters& oc, int lane) {
+  if (lane == 0) {
+    Ctrl* c = v.ctrl;
+    if (oc.added) atomicAdd(&c->size, static_cast<unsigned long long>(oc.added));
+    if (oc.claim) atomicAdd(&c->stats[kStClaimedSlow], static_cast<unsigned long long>(oc.claim));
+    if (oc.rounds) atomicAdd(&c->stats[kStEvictRounds], static_cast<unsigned long long>(oc.rounds));
+    if (oc.locks) atomicAdd(&c->stats[kStLockAcquired], static_cast<unsigned long long>(oc.locks));
+    if (oc.to) {
+      atomicAdd(&c->stats[kStLockTimeouts], static_cast<unsigned long long>(oc.to));
+      atomicOr(&c->err, kErrTimeout);
+    }
+    if (oc.stash) atomicAdd(&c->stats[kStStashed], static_cast<unsigned long long>(oc.stash));
+    if (oc.pend) atomicAdd(&c->stats[kStPending], static_cast<unsigned long long>(oc.pend));
+  }
+  oc = OvfCounters();
+}
+
+// Steps 3-4 for one insert whose candidate buckets were full (warp-wide).
+// `idx` is the caller's op index (kNoOp for a word moved by a merge); the
+// outcome goes to status[idx].  With `resizable`, an insert that finds no room
+// at all joins the pending list, else it is reported FULL.
+__device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uint32_t idx,
+                                              uint32_t seg, uint8_t* status, int resizable,
+                                              const List& pend, OvfCounters& oc, int lane) {
+  const uint32_t key0 = key_of(word0);
+  const uint32_t b1 = lh_bucket(bithash1(key0), v.M, v.p);
+  const uint32_t b2 = lh_bucket(bithash2(key0), v.M, v.p);
+
+  // 0: needs eviction, 1: placed, 2: stashed, 3: no room (pending)
+  int outcome = 0;
+  if (lane == 0) {
+    if (claim_cas(v, b1, word0) || (b2 != b1 && claim_cas(v, b2, word0))) {
+      outcome = 1;
+      ++oc.claim;
+    } else if (!stash_reserve(v)) {
+      outcome = 3;
+    }
+  }
+  outcome = __shfl_sync(kFull, outcome, 0);
+
+  if (outcome == 0) {
+    uint64_t cur = word0;
+    uint32_t b = b1;
+    bool placed = false;
+    for (uint32_t r = 0; r < v.max_evictions; ++r) {
+      // Look ahead: each lane checks whether the word in its slot could move
+      // to its other candidate bucket without a further eviction.
+      const uint64_t w = ld_relaxed64(v.buckets + static_cast<uint64_t>(b) * kSlots + lane);
+      bool good = false;
+      if (w != kEmptyWord) {
+        const uint32_t k = key_of(w);
+        const uint32_t a1 = lh_bucket(bithash1(k), v.M, v.p);
+        const uint32_t a2 = lh_bucket(bithash2(k), v.M, v.p);
+        const uint32_t alt = (a1 == b) ? a2 : a1;
+        if (alt != b) good = ld_relaxed32(v.masks + alt) != 0u;
+      }
+      const unsigned gm = __ballot_sync(kFull, good);
+      int res = 0;  // 0: evicted `victim`, 1: placed, 2: lock wait gave up
+      uint64_t victim = kEmptyWord;
+      if (lane == 0) {
+        ++oc.rounds;
+        const uint32_t vs = gm ? static_cast<uint32_t>(__ffs(gm) - 1)
+                               : ((bithash2(key_of(cur)) + r) & (kSlots - 1));
+        if (!lock_bucket(v, b)) {
+          res = 2;
+          ++oc.to;
+        } else {
+          ++oc.locks;
+          if (claim_cas(v, b, cur)) {
+            res = 1;
+          } else {
+            victim = atomicExch(ull(v.buckets + static_cast<uint64_t>(b) * kSlots + vs), cur);
+            res = (victim == kEmptyWord) ? 1 : 0;
+          }
+          unlock_bucket(v, b);
+        }
+      }
+      res = __shfl_sync(kFull, res, 0);
+      victim = __shfl_sync(kFull, victim, 0);
+      if (res == 1) {
+        placed = true;
+        break;
+      }
+      if (res == 2) break;
+      // Re-route the displaced word to its alternate bucket.
+      cur = victim;
+      const uint32_t kc = key_of(cur);
+      const uint32_t a1 = lh_bucket(bithash1(kc), v.M, v.p);
+      const uint32_t a2 = lh_bucket(bithash2(kc), v.M, v.p);
+      const uint32_t nb = (a1 == b) ? a2 : a1;
+      if (nb == b) break;  // both candidates are this bucket: no alternative
+      b = nb;
+      int ok = 0;
+      if (lane == 0) ok = claim_cas(v, b, cur);
+      if (__shfl_sync(kFull, ok, 0)) {
+        placed = true;
+        break;
+      }
+    }
+    if (lane == 0) {
+      if (placed) {
+        atomicSub(&v.ctrl->stash_claims, 1u);
+      } else {
+        const unsigned pos = atomicAdd(&v.ctrl->stash_tail, 1u);
+        st_relaxed64(v.stash_kv + pos, cur);
+        ++oc.stash;
+      }
+    }
+    outcome = placed ? 1 : 2;
+  }
+
+  if (lane == 0) {
+    if (outcome == 3) {
+      ++oc.pend;
+      if (resizable) {
+        const unsigned pos = atomicAdd(pend.count, 1u);
+        pend.words[pos] = word0;
+        pend.idx[pos] = idx;
+        if (pend.seg) pend.seg[pos] = seg;
+      } else {
+        atomicOr(&v.ctrl->err, kErrFull);
+        if (status && idx != kNoOp) status[idx] = ST_FULL;
+      }
+    } else if (idx != kNoOp) {
+      ++oc.added;
+      if (status) status[idx] = ST_INSERTED;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kOvfThreads)
     k_overflow(View v, List in, List pend, int resizable, uint8_t* __restrict__ status) {
   const int lane = threadIdx.x & 31;
   const unsigned warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
   const unsigned total = *in.count;
-  unsigned c_claim = 0, c_rounds = 0, c_locks = 0, c_to = 0, c_stash = 0, c_pend = 0, c_new = 0;
-
-  for (unsigned it = warp0; it < total; it += nwarps) {
-    const uint64_t word0 = in.words[it];
-    const uint32_t idx = in.idx[it];
-    const uint32_t key0 = key_of(word0);
-    const uint32_t b1 = lh_bucket(bithash1(key0), v.M, v.p);
-    const uint32_t b2 = lh_bucket(bithash2(key0), v.M, v.p);
-
-    // 0: needs eviction, 1: placed, 2: stashed, 3: no room (pending)
-    int outcome = 0;
-    if (lane == 0) {
-      if (claim_cas(v, b1, word0) || (b2 != b1 && claim_cas(v, b2, word0))) {
-        outcome = 1;
-        ++c_claim;
-      } else if (!stash_reserve(v)) {
-        outcome = 3;
-      }
-    }
-    outcome = __shfl_sync(kFull, outcome, 0);
-
-    if (outcome == 0) {
-      uint64_t cur = word0;
-      uint32_t b = b1;
-      bool placed = false;
-      for (uint32_t r = 0; r < v.max_evictions; ++r) {
-        // Look ahead: each lane checks whether the word in its slot could move
-        // to its other candidate bucket without a further eviction.
-        const uint64_t w = ld_relaxed64(v.buckets + static_cast<uint64_t>(b) * kSlots + lane);
-        bool good = false;
-        if (w != kEmptyWord) {
-          const uint32_t k = key_of(w);
-          const uint32_t a1 = lh_bucket(bithash1(k), v.M, v.p);
-          const uint32_t a2 = lh_bucket(bithash2(k), v.M, v.p);
-          const uint32_t alt = (a1 == b) ? a2 : a1;
-          if (alt != b) good = ld_relaxed32(v.masks + alt) != 0u;
-        }
-        const unsigned gm = __ballot_sync(kFull, good);
-        int res = 0;  // 0: evicted `victim`, 1: placed, 2: lock wait gave up
-        uint64_t victim = kEmptyWord;
-        if (lane == 0) {
-          ++c_rounds;
-          const uint32_t vs = gm ? static_cast<uint32_t>(__ffs(gm) - 1)
-                                 : ((bithash2(key_of(cur)) + r) & (kSlots - 1));
-          if (!lock_bucket(v, b)) {
-            res = 2;
-            ++c_to;
-          } else {
-            ++c_locks;
-            if (claim_cas(v, b, cur)) {
-              res = 1;
-            } else {
-              victim = atomicExch(ull(v.buckets + static_cast<uint64_t>(b) * kSlots + vs), cur);
-              res = (victim == kEmptyWord) ? 1 : 0;
-            }
-            unlock_bucket(v, b);
-          }
-        }
-        res = __shfl_sync(kFull, res, 0);
-        victim = __shfl_sync(kFull, victim, 0);
-        if (res == 1) {
-          placed = true;
-          break;
-        }
-        if (res == 2) break;
-        // Re-route the displaced word to its alternate bucket.
-        cur = victim;
-        const uint32_t kc = key_of(cur);
-        const uint32_t a1 = lh_bucket(bithash1(kc), v.M, v.p);
-        const uint32_t a2 = lh_bucket(bithash2(kc), v.M, v.p);
-        const uint32_t nb = (a1 == b) ? a2 : a1;
-        if (nb == b) break;  // both candidates are this bucket: no alternative
-        b = nb;
-        int ok = 0;
-        if (lane == 0) ok = claim_cas(v, b, cur);
-        if (__shfl_sync(kFull, ok, 0)) {
-          placed = true;
-          break;
-        }
-      }
-      if (lane == 0) {
-        if (placed) {
-          atomicSub(&v.ctrl->stash_claims, 1u);
-        } else {
-          const unsigned pos = atomicAdd(&v.ctrl->stash_tail, 1u);
-          st_relaxed64(v.stash_kv + pos, cur);
-          ++c_stash;
-        }
-      }
-      outcome = placed ? 1 : 2;
-    }
-
-    if (lane == 0) {
-      if (outcome == 3) {
-        ++c_pend;
-        if (resizable) {
-          const unsigned pos = atomicAdd(pend.count, 1u);
-          pend.words[pos] = word0;
-          pend.idx[pos] = idx;
-        } else {
-          atomicOr(&v.ctrl->err, kErrFull);
-          if (status && idx != kNoOp) status[idx] = ST_FULL;
-        }
-      } else if (idx != kNoOp) {
-        ++c_new;
-        if (status) status[idx] = ST_INSERTED;
-      }
-    }
-  }
-
-  if (lane == 0) {
-    Ctrl* c = v.ctrl;
-    if (c_new) atomicAdd(&c->size, static_cast<unsigned long long>(c_new));
-    if (c_claim) atomicAdd(&c->stats[kStClaimedSlow], static_cast<unsigned long long>(c_claim));
-    if (c_rounds) atomicAdd(&c->stats[kStEvictRounds], static_cast<unsigned long long>(c_rounds));
-    if (c_locks) atomicAdd(&c->stats[kStLockAcquired], static_cast<unsigned long long>(c_locks));
-    if (c_to) {
-      atomicAdd(&c->stats[kStLockTimeouts], static_cast<unsigned long long>(c_to));
-      atomicOr(&c->err, kErrTimeout);
-    }
-    if (c_stash) atomicAdd(&c->stats[kStStashed], static_cast<unsigned long long>(c_stash));
-    if (c_pend) atomicAdd(&c->stats[kStPending], static_cast<unsigned long long>(c_pend));
-  }
+  OvfCounters oc;
+  for (unsigned it = warp0; it < total; it += nwarps)
+    overflow_item(v, in.words[it], in.idx[it], 0, status, resizable, pend, oc, lane);
+  flush_ovf_counters(v, oc, lane);
 }
 
 // ----------------------------------------------------------------------------
@@ -643,8 +683,9 @@ __device__ void block_bitonic(uint64_t* a, unsigned P) {
   }
 }
 
-__global__ void __launch_bounds__(kMaintThreads) k_maint(View v) {
-  extern __shared__ uint64_t smem[];
+// One CTA maintains the stash of the table of `v`; `smem` holds
+// kMaintSmemWords words.
+__device__ void maint_body(const View& v, uint64_t* smem) {
   __shared__ unsigned s_reins, s_live;
   Ctrl* c = v.ctrl;
   const unsigned tail = c->stash_tail;
@@ -714,6 +755,11 @@ __global__ void __launch_bounds__(kMaintThreads) k_maint(View v) {
   }
 }
 
+__global__ void __launch_bounds__(kMaintThreads) k_maint(View v) {
+  extern __shared__ uint64_t smem[];
+  maint_body(v, smem);
+}
+
 // ----------------------------------------------------------------------------
 // Linear-hashing resize (Section IV-C)
 // ----------------------------------------------------------------------------
@@ -723,11 +769,7 @@ __global__ void __launch_bounds__(kMaintThreads) k_maint(View v) {
 // when neither candidate address equals the source under the new state; it
 // then belongs to the partner, where the movers are packed from slot 0 by a
 // ballot-rank compaction.
-__global__ void __launch_bounds__(256) k_split(View v, uint32_t src0, uint32_t count, uint32_t half) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= count) return;
-  const uint32_t src = src0 + w;
+__device__ __forceinline__ void split_pair(const View& v, uint32_t src, uint32_t half, int lane) {
   const uint32_t dst = src + half;
   uint64_t* sb = v.buckets + static_cast<uint64_t>(src) * kSlots;
   uint64_t* db = v.buckets + static_cast<uint64_t>(dst) * kSlots;
@@ -749,6 +791,12 @@ __global__ void __launch_bounds__(256) k_split(View v, uint32_t src0, uint32_t c
     const int nm = __popc(mm);
     v.masks[dst] = nm >= 32 ? 0u : (0xFFFFFFFFu << nm);
   }
+}
+
+__global__ void __launch_bounds__(256) k_split(View v, uint32_t src0, uint32_t count, uint32_t half) {
+  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= count) return;
+  split_pair(v, src0 + w, half, threadIdx.x & 31);
 }
 
 // Contraction pre-check: how many words of the batch's high buckets do not
@@ -821,6 +869,109 @@ __global__ void k_count_inserts(const uint8_t* __restrict__ ops, uint64_t n, uns
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// ----------------------------------------------------------------------------
+// Multi-table batches: many independent tables serviced by one launch per
+// phase.  A batch is a list of segments (table, op range); segment s owns the
+// 32-op chunks [chunk0_s, chunk0_{s+1}) of the batch.  Each table keeps its own
+// control block, so counters, stash and sticky errors stay per table.
+// ----------------------------------------------------------------------------
+
+__device__ __forceinline__ OpPtrs seg_ptrs(const MultiSeg& S) {
+  return OpPtrs{S.ops, S.keys, S.vals, S.vals_out, nullptr, S.status};
+}
+
+// Each warp takes a contiguous run of chunks, so it changes table only at
+// segment boundaries and flushes its counters there.
+__global__ void __launch_bounds__(kOpsThreads, HIVE_MULTI_MIN_BLOCKS)
+    k_multi_ops(const MultiHdr* __restrict__ hdr, const MultiSeg* __restrict__ segs,
+                const View* __restrict__ views, List ovf) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t total = hdr->total_chunks;
+  const uint32_t ns = hdr->n_segs;
+  const uint32_t c0 = static_cast<uint32_t>(static_cast<uint64_t>(total) * w / nw);
+  const uint32_t c1 = static_cast<uint32_t>(static_cast<uint64_t>(total) * (w + 1) / nw);
+  if (c0 >= c1) return;
+  uint32_t lo = 0, hi = ns;  // last segment with chunk0 <= c0
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (segs[mid].chunk0 <= c0) lo = mid; else hi = mid;
+  }
+  uint32_t s = lo;
+  View v = views[segs[s].table];
+  uint32_t stash_n = v.ctrl->stash_n;
+  OpPtrs a = seg_ptrs(segs[s]);
+  LaneCounters cnt;
+  for (uint32_t c = c0; c < c1; ++c) {
+    if (s + 1 < ns && segs[s + 1].chunk0 <= c) {
+      flush_counters(v, cnt, lane);
+      do {
+        ++s;
+      } while (s + 1 < ns && segs[s + 1].chunk0 <= c);
+      v = views[segs[s].table];
+      stash_n = v.ctrl->stash_n;
+      a = seg_ptrs(segs[s]);
+    }
+    run_chunk<kModeMixed>(v, stash_n, a, c - segs[s].chunk0, segs[s].n, ovf, s, cnt, lane);
+  }
+  flush_counters(v, cnt, lane);
+}
+
+// Steps 3-4 for the overflow list of a multi-table batch.  Inserts that find
+// no room are reported FULL (a resizable table grows before its next batch).
+__global__ void __launch_bounds__(kOvfThreads)
+    k_multi_overflow(const MultiSeg* __restrict__ segs, const View* __restrict__ views, List in) {
+  const int lane = threadIdx.x & 31;
+  const unsigned warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  const unsigned total = *in.count;
+  const List none{nullptr, nullptr, nullptr, nullptr};
+  for (unsigned it = warp0; it < total; it += nwarps) {
+    const uint32_t sg = in.seg[it];
+    const View v = views[segs[sg].table];
+    OvfCounters oc;
+    overflow_item(v, in.words[it], in.idx[it], sg, segs[sg].status, 0, none, oc, lane);
+    flush_ovf_counters(v, oc, lane);
+  }
+}
+
+// One CTA per table: stash maintenance (exits at once when nothing changed).
+__global__ void __launch_bounds__(256) k_multi_maint(const View* __restrict__ views) {
+  extern __shared__ uint64_t smem[];
+  maint_body(views[blockIdx.x], smem);
+}
+
+// One wave of split launches over many tables: warp w runs pair
+// w - pair0 of the job whose range holds w.  Jobs of one wave touch disjoint
+// buckets (a table appears in a wave with splits of one round only).
+__global__ void __launch_bounds__(256)
+    k_multi_split(const MultiJob* __restrict__ jobs, uint32_t n_jobs, uint32_t total_pairs,
+                  const View* __restrict__ views) {
+  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= total_pairs) return;
+  uint32_t lo = 0, hi = n_jobs;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (jobs[mid].pair0 <= w) lo = mid; else hi = mid;
+  }
+  const MultiJob J = jobs[lo];
+  View v = views[J.table];
+  v.M = J.M;
+  v.p = J.p;
+  split_pair(v, J.src0 + (w - J.pair0), J.half, threadIdx.x & 31);
+}
+
+// Per-table size and stash fill after a batch, for the host's resize policy.
+__global__ void k_multi_gather(const View* __restrict__ views, uint32_t n_tables,
+                               unsigned long long* __restrict__ out) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tables) return;
+  const Ctrl* c = views[t].ctrl;
+  out[2 * t] = c->size;
+  out[2 * t + 1] = (static_cast<unsigned long long>(c->err) << 32) | c->stash_claims;
+}
+
 template <int MODE>
 cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys,
                          const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
@@ -831,8 +982,8 @@ cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys
   const uint64_t cap = static_cast<uint64_t>(L.num_sms) * L.ops_blocks_per_sm;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
-  k_ops<MODE><<<static_cast<unsigned>(blocks), kOpsThreads, 0, s>>>(v, ops, keys, vals, n,
-                                                                     vals_out, found, status, ovf);
+  const OpPtrs a{ops, keys, vals, vals_out, found, status};
+  k_ops<MODE><<<static_cast<unsigned>(blocks), kOpsThreads, 0, s>>>(v, a, n, ovf);
   return cudaGetLastError();
 }
 
@@ -895,6 +1046,41 @@ cudaError_t launch_count_inserts(const uint8_t* ops, uint64_t n, unsigned* out, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_multi_ops(const MultiHdr* hdr, const MultiSeg* segs, const View* views, List ovf,
+                             const Launch& L, cudaStream_t s) {
+  k_multi_ops<<<static_cast<unsigned>(L.num_sms * L.multi_blocks_per_sm), kOpsThreads, 0, s>>>(
+      hdr, segs, views, ovf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_overflow(const MultiSeg* segs, const View* views, List in,
+                                  const Launch& L, cudaStream_t s) {
+  k_multi_overflow<<<static_cast<unsigned>(L.num_sms * L.ovf_blocks_per_sm), kOvfThreads, 0, s>>>(
+      segs, views, in);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_maint(const View* views, uint32_t n_tables, cudaStream_t s) {
+  if (!n_tables) return cudaSuccess;
+  k_multi_maint<<<n_tables, 256, kMaintSmemWords * sizeof(uint64_t), s>>>(views);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_split(const MultiJob* jobs, uint32_t n_jobs, uint32_t total_pairs,
+                               const View* views, cudaStream_t s) {
+  if (!total_pairs) return cudaSuccess;
+  const unsigned blocks = static_cast<unsigned>((static_cast<uint64_t>(total_pairs) * 32 + 255) / 256);
+  k_multi_split<<<blocks, 256, 0, s>>>(jobs, n_jobs, total_pairs, views);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_gather(const View* views, uint32_t n_tables, unsigned long long* out,
+                                cudaStream_t s) {
+  if (!n_tables) return cudaSuccess;
+  k_multi_gather<<<(n_tables + 255) / 256, 256, 0, s>>>(views, n_tables, out);
+  return cudaGetLastError();
+}
+
 cudaError_t query_occupancy(Launch* L) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -905,9 +1091,15 @@ cudaError_t query_occupancy(Launch* L) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeInsert>, kOpsThreads, 0);
   if (e != cudaSuccess) return e;
   L->ops_blocks_per_sm = b > 0 ? b : 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_multi_ops, kOpsThreads, 0);
+  if (e != cudaSuccess) return e;
+  L->multi_blocks_per_sm = b > 0 ? b : 1;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_overflow, kOvfThreads, 0);
   if (e != cudaSuccess) return e;
   L->ovf_blocks_per_sm = b > 0 ? (b < 2 ? b : 2) : 1;
+  e = cudaFuncSetAttribute(k_multi_maint, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kMaintSmemWords * sizeof(uint64_t)));
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_maint, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(kMaintSmemWords * sizeof(uint64_t)));
 }

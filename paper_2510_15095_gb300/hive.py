@@ -29,7 +29,8 @@ PLACE_BALANCED, PLACE_FIRST = 0, 1
 EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", "hive_find",
            "hive_erase", "hive_execute", "hive_size", "hive_capacity", "hive_clear", "hive_check",
            "hive_stats", "hive_dump", "hive_profile_enable", "hive_profile_read",
-           "hive_insert_noalloc", "hive_last_error"]
+           "hive_insert_noalloc", "hive_multi_create", "hive_multi_execute",
+           "hive_multi_destroy", "hive_last_error"]
 KERNEL_KINDS = ["find", "insert", "erase", "mixed", "evict", "maint", "split", "merge", "count"]
 
 
@@ -58,6 +59,12 @@ class Stats(C.Structure):
 
 class Profile(C.Structure):
     _fields_ = [("ms", C.c_double * 16), ("launches", C.c_uint64 * 16)]
+
+
+class Segment(C.Structure):
+    _fields_ = [("table", C.c_uint32), ("reserved0", C.c_uint32), ("n", C.c_uint64),
+                ("n_insert", C.c_uint64), ("ops", C.c_void_p), ("keys", C.c_void_p),
+                ("vals", C.c_void_p), ("vals_out", C.c_void_p), ("status", C.c_void_p)]
 
 
 class Image(C.Structure):
@@ -98,6 +105,10 @@ def load_library(path: str = LIB_PATH):
         L.hive_stats.argtypes = [vp, C.POINTER(Stats), vp]
         L.hive_dump.argtypes = [vp, C.POINTER(Image), vp]
         L.hive_insert_noalloc.argtypes = [vp, vp, vp, u64, vp, vp]
+        L.hive_multi_create.argtypes = [C.POINTER(vp), C.c_uint32, C.c_uint32, u64, i32, vp,
+                                        C.POINTER(vp)]
+        L.hive_multi_execute.argtypes = [vp, C.POINTER(Segment), C.c_uint32, vp]
+        L.hive_multi_destroy.argtypes = [vp]
         L.hive_profile_enable.argtypes = [vp, i32]
         L.hive_profile_read.argtypes = [vp, C.POINTER(Profile)]
         L.hive_last_error.argtypes = []
@@ -307,6 +318,49 @@ class HiveTable:
         return {"nb": nb, "S": S, "M": int(img.M), "p": int(img.p), "buckets": b, "masks": m,
                 "locks": lk, "stash": st[: int(img.stash_n)], "stash_cap": int(img.stash_cap),
                 "size": int(img.size), "pending": int(img.pending)}
+
+
+class HiveMulti:
+    """A group of tables serviced by one launch per phase (hive_multi_*)."""
+
+    def __init__(self, tables, max_segments: int, max_ops: int, use_graph: bool = True,
+                 stream=None):
+        self._L = load_library()
+        self.tables = list(tables)
+        arr = (C.c_void_p * len(self.tables))(*[t._h.value for t in self.tables])
+        h = C.c_void_p()
+        _raise(self._L, self._L.hive_multi_create(arr, len(self.tables), int(max_segments),
+                                                  int(max_ops), 1 if use_graph else 0,
+                                                  _stream_ptr(stream), C.byref(h)))
+        self._h = h
+
+    def execute(self, segments, stream=None):
+        """segments: iterable of dicts with keys table, ops, keys and optionally
+        vals, vals_out, status (CUDA tensors) and n_insert (int)."""
+        segs = list(segments)
+        arr = (Segment * max(len(segs), 1))()
+        for i, g in enumerate(segs):
+            n = g["keys"].numel()
+            arr[i].table = int(g["table"])
+            arr[i].n = n
+            arr[i].n_insert = int(g.get("n_insert", n))
+            arr[i].ops = _dptr(g["ops"], 1, n, "ops")
+            arr[i].keys = _dptr(g["keys"], 4, n, "keys")
+            arr[i].vals = _dptr(g.get("vals"), 4, n, "vals")
+            arr[i].vals_out = _dptr(g.get("vals_out"), 4, n, "vals_out")
+            arr[i].status = _dptr(g.get("status"), 1, n, "status")
+        _raise(self._L, self._L.hive_multi_execute(self._h, arr, len(segs), _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.hive_multi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def to_device_u32(a: np.ndarray, device="cuda"):

@@ -245,3 +245,75 @@ def mixed_batch(rng: np.random.Generator, live_keys: np.ndarray, new_keys: np.nd
     vals = np.concatenate([values_for(ins, seed), np.zeros(n_erase + n_find, U32)]).astype(U32)
     order = rng.permutation(ops.size)
     return ops[order], keys[order], vals[order]
+
+
+# ----------------------------------------------------------------------------
+# The same generators on torch tensors (CUDA or CPU), for large workloads that
+# are generated where they are used.  Same seeds give the same keys as above.
+# ----------------------------------------------------------------------------
+
+def _mul32_t(x, c: int):
+    """(x * c) mod 2^32 for int64 tensors holding values < 2^32, overflow-free."""
+    lo = x & 0xFFFF
+    hi = x >> 16
+    return (lo * c + (((hi * c) & 0xFFFF) << 16)) & MASK32
+
+
+def feistel_bits_t(x, seed: int, bits: int):
+    assert bits % 2 == 0 and 2 <= bits <= 32
+    half = bits // 2
+    hm = (1 << half) - 1
+    left = (x >> half) & hm
+    right = x & hm
+    for k in _round_keys(seed):
+        f = (right ^ (k & hm)) & hm
+        f = (_mul32_t(f, 0x2C1B3C6D) + (k >> 7)) & MASK32
+        f = f ^ (f >> 15)
+        f = _mul32_t(f, 0x297A2D39)
+        f = f ^ (f >> 12)
+        left, right = right, left ^ (f & hm)
+    return (left << half) | right
+
+
+def splitmix32_t(x):
+    z = (x + 0x9E3779B9) & MASK32
+    z = _mul32_t(z ^ (z >> 16), 0x85EBCA6B)
+    z = _mul32_t(z ^ (z >> 13), 0xC2B2AE35)
+    return z ^ (z >> 16)
+
+
+def multi_table_step(torch, seed: int, count: int, n_ops: int, device, absent_base=1 << 31):
+    """One step's mixed ops for one table whose inserted keys are the stream
+    positions [0, count) of `seed`: insert:find:erase = 2:1:1 of n_ops.  Inserts
+    take the next positions; erases and finds each take half live keys (distinct
+    positions of a random permutation, so no key is both updated and searched)
+    and half absent keys (positions at absent_base and above, never inserted,
+    erases and finds in disjoint halves).  Returns (ops u8, keys i32, vals i32,
+    new count, n_insert)."""
+    g = torch.Generator(device=device)
+    g.manual_seed((seed * 1000003 + count) & 0x7FFFFFFFFFFF)
+    n_ins = n_ops // 2
+    n_fd = n_ops // 4
+    n_er = n_ops - n_ins - n_fd
+    er_live = min(n_er // 2, count)
+    fd_live = min(n_fd // 2, count - er_live)
+    perm = torch.randperm(count, generator=g, device=device)[: er_live + fd_live] if count else \
+        torch.zeros(0, dtype=torch.int64, device=device)
+    ins_pos = torch.arange(count, count + n_ins, device=device, dtype=torch.int64)
+    er_abs = n_er - er_live
+    fd_abs = n_fd - fd_live
+    quarter = 1 << 29
+    er_abs_pos = absent_base + torch.randperm(quarter, generator=g, device=device)[:er_abs] \
+        if er_abs else torch.zeros(0, dtype=torch.int64, device=device)
+    fd_abs_pos = absent_base + quarter + torch.randint(0, quarter, (fd_abs,), generator=g,
+                                                       device=device)
+    pos = torch.cat([ins_pos, perm[:er_live], er_abs_pos, perm[er_live:], fd_abs_pos])
+    ops = torch.cat([torch.full((n_ins,), OP_INSERT, dtype=torch.uint8, device=device),
+                     torch.full((er_live + er_abs,), OP_ERASE, dtype=torch.uint8, device=device),
+                     torch.full((fd_live + fd_abs,), OP_FIND, dtype=torch.uint8, device=device)])
+    keys = feistel_bits_t(pos, seed, 32)
+    vals = splitmix32_t(keys ^ (seed & MASK32))
+    vals = torch.where(ops == OP_INSERT, vals, torch.zeros_like(vals))
+    order = torch.randperm(ops.numel(), generator=g, device=device)
+    to32 = lambda t: (t - ((t >> 31) << 32)).to(torch.int32)  # noqa: E731  two's complement view
+    return ops[order], to32(keys[order]), to32(vals[order]), count + n_ins, n_ins
