@@ -52,6 +52,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 22,
                     help="inserts (and as many finds) in the CPU oracle sample")
+    ap.add_argument("--no-tables", action="store_true", help="skip the multi-table leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--tables-n", type=int, default=1024)
+    ap.add_argument("--tables-steps", type=int, default=8)
+    ap.add_argument("--serving-requests", type=int, default=3000)
     return ap.parse_args()
 
 
@@ -229,6 +234,149 @@ def run_reference(args, rank):
                              "sample": sample},
             "e2e": {"value": v, "unit": "Gops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# multi-table leg: many independent tables, one batched launch per step
+# ---------------------------------------------------------------------------
+
+def tables_leg(torch, H, dev, n_tables=1024, steps=8, seed=40):
+    """1024 resizable tables with initial capacities log-uniform in
+    [2^10, 2^22] slots, preloaded to half load; per step every table gets a
+    mixed batch of log-uniform [2^6, 2^20] ops (insert:find:erase 2:1:1).
+    The same steps run once as one multi-table batch per step (CUDA graph
+    replay) and once as one hive_execute per table per step, on two equal sets
+    of tables; outputs must be identical."""
+    from paper_2510_15095_gb300 import workload as W
+    rng = np.random.default_rng(seed)
+    caps = (np.exp(rng.uniform(10, 22, n_tables) * np.log(2)).astype(np.int64) // 32 + 1) * 32
+    nops = np.exp(rng.uniform(6, 20, (steps, n_tables)) * np.log(2)).astype(np.int64)
+    K = 1024
+    ins_total = nops.sum(axis=0) // 2
+    max_slots = caps + (ins_total * 10 // 9) + caps // 2 + 64 * K
+    sets = []
+    for _ in range(2):
+        tabs = []
+        for t in range(n_tables):
+            tb = H.HiveTable(int(caps[t]), max_slots=int(max_slots[t]), resizable=True,
+                             resize_batch=K)
+            k, v = W.preload_t(torch, 7000 + t, int(caps[t]) // 2, dev)
+            tb.insert(k, v, status=False)
+            tabs.append(tb)
+        sets.append(tabs)
+    counts = [int(c) // 2 for c in caps]
+    work = []
+    for st in range(steps):
+        row = []
+        for t in range(n_tables):
+            ops, keys, vals, counts[t], n_ins = W.mixed_step_t(torch, 7000 + t, counts[t],
+                                                                int(nops[st, t]), dev, salt=st)
+            row.append((ops, keys, vals, n_ins))
+        work.append(row)
+    outs = [[(torch.empty(w[1].numel(), dtype=torch.int32, device=dev),
+              torch.empty(w[1].numel(), dtype=torch.uint8, device=dev)) for w in row] for row in work]
+    max_ops = int(nops.sum(axis=1).max()) + 1
+    multi = H.HiveMulti(sets[0], max_segments=n_tables, max_ops=max_ops, use_graph=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for st in range(steps):
+        multi.execute([{"table": t, "ops": w[0], "keys": w[1], "vals": w[2], "n_insert": w[3],
+                        "vals_out": outs[st][t][0], "status": outs[st][t][1]}
+                       for t, w in enumerate(work[st])])
+    torch.cuda.synchronize(dev)
+    t_multi = time.perf_counter() - t0
+    plain_out = []
+    t0 = time.perf_counter()
+    for st in range(steps):
+        for t, w in enumerate(work[st]):
+            plain_out.append(sets[1][t].execute(w[0], w[1], w[2]))
+    torch.cuda.synchronize(dev)
+    t_plain = time.perf_counter() - t0
+    same = all(torch.equal(outs[st][t][0], plain_out[st * n_tables + t][0]) and
+               torch.equal(outs[st][t][1], plain_out[st * n_tables + t][1])
+               for st in range(steps) for t in range(n_tables))
+    caps_same = all(a.capacity() == b.capacity() for a, b in zip(*sets))
+    ops_total = int(nops.sum())
+    multi.close()
+    for tabs in sets:
+        for tb in tabs:
+            tb.close()
+    return {"workload": (f"{n_tables} resizable tables, capacities log-uniform 2^10-2^22 slots "
+                         f"(half full), {steps} steps of log-uniform 2^6-2^20 ops per table "
+                         "(insert:find:erase 2:1:1)"),
+            "ops": ops_total, "batched_gops": ops_total / t_multi / 1e9,
+            "plain_gops": ops_total / t_plain / 1e9, "speedup": t_plain / t_multi,
+            "batched_s": t_multi, "plain_s": t_plain, "identical_results": bool(same),
+            "identical_capacity": bool(caps_same), "graph": True}
+
+
+# ---------------------------------------------------------------------------
+# serving leg: continuous batching vs one launch per request
+# ---------------------------------------------------------------------------
+
+def serving_leg(torch, H, dev, n_tables=64, n_requests=3000, seed=50):
+    """64 resizable tables preloaded with 2^16 keys; requests of log-uniform
+    [1, 2^20] ops (insert:erase:find 40/20/40) on uniform random tables.
+    First both servers run closed-loop (every request available at once) to
+    find their saturation throughput; then Poisson arrivals at 70% of the
+    batched server's saturation request rate measure p50/p99 latency of both."""
+    from paper_2510_15095_gb300 import serving as SV
+    from paper_2510_15095_gb300 import workload as W
+    pre = 1 << 16
+
+    def fresh():
+        tabs = []
+        for t in range(n_tables):
+            tb = H.HiveTable(1 << 17, max_slots=1 << 23, resizable=True, resize_batch=1024)
+            k, v = W.preload_t(torch, 1000 + t, pre, dev)
+            tb.insert(k, v, status=False)
+            tabs.append(tb)
+        return tabs
+
+    counts = [pre] * n_tables
+    base = SV.make_trace(torch, n_tables, n_requests, rate_per_s=1.0, seed=seed, counts=counts,
+                         max_log2_ops=20, device=dev)
+
+    def with_arrivals(arr):
+        return [SV.Request(r.rid, r.table, float(a), r.ops, r.keys, r.vals, r.n_insert)
+                for r, a in zip(base, arr)]
+
+    def serve(reqs, fifo):
+        tabs = fresh()
+        torch.cuda.synchronize(dev)
+        if fifo:
+            out = SV.run_fifo(tabs, reqs)
+        else:
+            srv = SV.HiveServer(tabs, hbm_budget_bytes=64e9, max_batch_ops=1 << 23,
+                                max_batch_reqs=256, depth=2)
+            out = srv.run(reqs)
+            srv.close()
+        for tb in tabs:
+            tb.close()
+        return out
+
+    zeros = np.zeros(n_requests)
+    sat_b_reqs = with_arrivals(zeros)
+    sat_b = serve(sat_b_reqs, False)
+    sat_f_reqs = with_arrivals(zeros)
+    sat_f = serve(sat_f_reqs, True)
+    same = all(torch.equal(a.status, b.status) and torch.equal(a.vals_out, b.vals_out)
+               for a, b in zip(sat_b_reqs, sat_f_reqs))
+    rate = 0.7 * n_requests / sat_b["makespan_s"]
+    gaps = np.random.default_rng(seed + 1).exponential(1.0 / rate, n_requests)
+    arr = np.cumsum(gaps) - gaps[0]
+    lat_b = serve(with_arrivals(arr), False)
+    lat_f = serve(with_arrivals(arr), True)
+    keep = ("p50_ms", "p99_ms", "mean_ms", "gops", "batches", "mean_batch_requests", "rejected")
+    return {"workload": (f"{n_tables} resizable tables preloaded with 2^16 keys, {n_requests} "
+                         "requests of log-uniform 1-2^20 ops (insert:erase:find 40/20/40), HBM "
+                         "budget 64 GB"),
+            "ops": int(sat_b["ops"]),
+            "saturation": {"batched_gops": sat_b["gops"], "fifo_gops": sat_f["gops"],
+                           "speedup": sat_b["gops"] / sat_f["gops"]},
+            "poisson_rate_req_per_s": rate,
+            "batched": {k: lat_b[k] for k in keep}, "fifo": {k: lat_f[k] for k in keep},
+            "identical_results": bool(same)}
 
 
 # ---------------------------------------------------------------------------
@@ -423,6 +571,13 @@ def main():
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
     assert bool((o_ff.numpy() == w["is_hit"]).all()), "e2e find flags disagree"
 
+    extra = {}
+    if not args.no_tables:
+        extra["multi_table"] = tables_leg(torch, H, dev, n_tables=args.tables_n,
+                                          steps=args.tables_steps)
+    if not args.no_serving:
+        extra["serving"] = serving_leg(torch, H, dev, n_requests=args.serving_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n = min(args.cpu_sample, n_ins)
@@ -437,7 +592,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "u32/u64", "data": "synthetic", "config": cfg, "phases": phases,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": gpu_launches}
+                "gpu_launches": gpu_launches, **extra}
         print(json.dumps(line), flush=True)
     t.close()
     if world > 1:

@@ -249,19 +249,29 @@ typedef struct {
   uint8_t* status;        /* [n] per-op status (device, nullable) */
 } hive_segment;
 
+/* Flags of hive_multi_create. */
+enum {
+  HIVE_MULTI_GRAPH = 1, /* capture the fixed kernel sequence into a CUDA graph on the
+                           first batch and replay it afterwards */
+  HIVE_MULTI_ASYNC = 2  /* never wait for a batch: resizable tables grow for an upper
+                           bound of their size (last gathered size + inserts queued
+                           since) and are not contracted; two batches may be in flight */
+};
+
 /* Groups tables (created by hive_create on the current device) for batched
- * calls.  max_segments and max_ops bound one batch; use_graph != 0 captures
- * the fixed kernel sequence into a CUDA graph on the first call and replays it
- * afterwards.  The tables stay owned by the caller and must outlive the
- * group; they may still be used one by one between batches (same stream). */
+ * calls.  max_segments and max_ops bound one batch.  The tables stay owned by
+ * the caller and must outlive the group.  Without HIVE_MULTI_ASYNC they may
+ * still be used one by one between batches (same stream); with it, drive them
+ * only through the group. */
 hive_status hive_multi_create(hive_table* const* tables, uint32_t n_tables,
-                              uint32_t max_segments, uint64_t max_ops, int use_graph,
+                              uint32_t max_segments, uint64_t max_ops, int flags,
                               void* stream, hive_multi** out);
 
 /* Runs one batch on `stream`.  Consecutive batches of one group go on one
- * stream.  With only fixed tables the call does not synchronise; with
- * resizable tables it waits once for the batch (to apply the contraction
- * policy to all tables).  Errors: INVALID_ARG (bad segment, too many ops,
+ * stream.  Without HIVE_MULTI_ASYNC, a group holding resizable tables waits
+ * once for the batch (exact sizes, contraction policy applied to its tables);
+ * otherwise the call returns after queueing, waiting only for the batch
+ * queued two calls earlier.  Errors: INVALID_ARG (bad segment, too many ops,
  * segments or split launches), CUDA. */
 hive_status hive_multi_execute(hive_multi* m, const hive_segment* segs, uint32_t n_segs,
                                void* stream);

@@ -110,7 +110,8 @@ struct MultiJob {
 };
 
 struct MultiHdr {
-  uint32_t n_segs, total_chunks, n_tables, pad;
+  uint32_t n_segs, total_chunks, n_tables;
+  uint32_t n_touched;  // distinct tables of the batch, listed after the views
 };
 
 enum OpMode : int { kModeFind = 0, kModeInsert = 1, kModeErase = 2, kModeMixed = 3 };
@@ -139,11 +140,12 @@ cudaError_t launch_multi_ops(const MultiHdr* hdr, const MultiSeg* segs, const Vi
                              const Launch& L, cudaStream_t s);
 cudaError_t launch_multi_overflow(const MultiSeg* segs, const View* views, List in,
                                   const Launch& L, cudaStream_t s);
-cudaError_t launch_multi_maint(const View* views, uint32_t n_tables, cudaStream_t s);
+cudaError_t launch_multi_maint(const MultiHdr* hdr, const View* views, const uint32_t* touched,
+                               uint32_t max_tables, cudaStream_t s);
 cudaError_t launch_multi_split(const MultiJob* jobs, uint32_t n_jobs, uint32_t total_pairs,
                                const View* views, cudaStream_t s);
-cudaError_t launch_multi_gather(const View* views, uint32_t n_tables, unsigned long long* out,
-                                cudaStream_t s);
+cudaError_t launch_multi_gather(const MultiHdr* hdr, const View* views, const uint32_t* touched,
+                                uint32_t max_tables, unsigned long long* out, cudaStream_t s);
 cudaError_t query_occupancy(Launch* L);
 
 }  // namespace hive

@@ -936,10 +936,15 @@ __global__ void __launch_bounds__(kOvfThreads)
   }
 }
 
-// One CTA per table: stash maintenance (exits at once when nothing changed).
-__global__ void __launch_bounds__(256) k_multi_maint(const View* __restrict__ views) {
+// One CTA per table of the batch: stash maintenance (exits at once when
+// nothing changed).  The grid covers every table of the group, so a captured
+// graph serves batches of any composition.
+__global__ void __launch_bounds__(256)
+    k_multi_maint(const MultiHdr* __restrict__ hdr, const View* __restrict__ views,
+                  const uint32_t* __restrict__ touched) {
   extern __shared__ uint64_t smem[];
-  maint_body(views[blockIdx.x], smem);
+  if (blockIdx.x >= hdr->n_touched) return;
+  maint_body(views[touched[blockIdx.x]], smem);
 }
 
 // One wave of split launches over many tables: warp w runs pair
@@ -962,11 +967,14 @@ __global__ void __launch_bounds__(256)
   split_pair(v, J.src0 + (w - J.pair0), J.half, threadIdx.x & 31);
 }
 
-// Per-table size and stash fill after a batch, for the host's resize policy.
-__global__ void k_multi_gather(const View* __restrict__ views, uint32_t n_tables,
+// Size and stash fill of each table of the batch, for the host's resize
+// policy (entries of tables outside the batch are left as they were).
+__global__ void k_multi_gather(const MultiHdr* __restrict__ hdr, const View* __restrict__ views,
+                               const uint32_t* __restrict__ touched,
                                unsigned long long* __restrict__ out) {
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_tables) return;
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= hdr->n_touched) return;
+  const uint32_t t = touched[j];
   const Ctrl* c = views[t].ctrl;
   out[2 * t] = c->size;
   out[2 * t + 1] = (static_cast<unsigned long long>(c->err) << 32) | c->stash_claims;
@@ -1060,9 +1068,10 @@ cudaError_t launch_multi_overflow(const MultiSeg* segs, const View* views, List 
   return cudaGetLastError();
 }
 
-cudaError_t launch_multi_maint(const View* views, uint32_t n_tables, cudaStream_t s) {
-  if (!n_tables) return cudaSuccess;
-  k_multi_maint<<<n_tables, 256, kMaintSmemWords * sizeof(uint64_t), s>>>(views);
+cudaError_t launch_multi_maint(const MultiHdr* hdr, const View* views, const uint32_t* touched,
+                               uint32_t max_tables, cudaStream_t s) {
+  if (!max_tables) return cudaSuccess;
+  k_multi_maint<<<max_tables, 256, kMaintSmemWords * sizeof(uint64_t), s>>>(hdr, views, touched);
   return cudaGetLastError();
 }
 
@@ -1074,10 +1083,10 @@ cudaError_t launch_multi_split(const MultiJob* jobs, uint32_t n_jobs, uint32_t t
   return cudaGetLastError();
 }
 
-cudaError_t launch_multi_gather(const View* views, uint32_t n_tables, unsigned long long* out,
-                                cudaStream_t s) {
-  if (!n_tables) return cudaSuccess;
-  k_multi_gather<<<(n_tables + 255) / 256, 256, 0, s>>>(views, n_tables, out);
+cudaError_t launch_multi_gather(const MultiHdr* hdr, const View* views, const uint32_t* touched,
+                                uint32_t max_tables, unsigned long long* out, cudaStream_t s) {
+  if (!max_tables) return cudaSuccess;
+  k_multi_gather<<<(max_tables + 255) / 256, 256, 0, s>>>(hdr, views, touched, out);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ ERRORS = {1: "INVALID_ARG", 2: "RESERVED_KEY", 3: "OOM", 4: "FULL", 5: "TIMEOUT"
 INSERTED, REPLACED, ERASED, NOT_FOUND, FOUND, FULL, RESERVED_KEY = range(7)
 OP_INSERT, OP_FIND, OP_ERASE = 0, 1, 2
 PLACE_BALANCED, PLACE_FIRST = 0, 1
+MULTI_GRAPH, MULTI_ASYNC = 1, 2
 
 EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", "hive_find",
            "hive_erase", "hive_execute", "hive_size", "hive_capacity", "hive_clear", "hive_check",
@@ -324,13 +325,14 @@ class HiveMulti:
     """A group of tables serviced by one launch per phase (hive_multi_*)."""
 
     def __init__(self, tables, max_segments: int, max_ops: int, use_graph: bool = True,
-                 stream=None):
+                 asynchronous: bool = False, stream=None):
         self._L = load_library()
         self.tables = list(tables)
         arr = (C.c_void_p * len(self.tables))(*[t._h.value for t in self.tables])
         h = C.c_void_p()
+        flags = (MULTI_GRAPH if use_graph else 0) | (MULTI_ASYNC if asynchronous else 0)
         _raise(self._L, self._L.hive_multi_create(arr, len(self.tables), int(max_segments),
-                                                  int(max_ops), 1 if use_graph else 0,
+                                                  int(max_ops), flags,
                                                   _stream_ptr(stream), C.byref(h)))
         self._h = h
 

@@ -282,29 +282,32 @@ def splitmix32_t(x):
     return z ^ (z >> 16)
 
 
-def multi_table_step(torch, seed: int, count: int, n_ops: int, device, absent_base=1 << 31):
-    """One step's mixed ops for one table whose inserted keys are the stream
-    positions [0, count) of `seed`: insert:find:erase = 2:1:1 of n_ops.  Inserts
-    take the next positions; erases and finds each take half live keys (distinct
-    positions of a random permutation, so no key is both updated and searched)
-    and half absent keys (positions at absent_base and above, never inserted,
-    erases and finds in disjoint halves).  Returns (ops u8, keys i32, vals i32,
-    new count, n_insert)."""
+def mixed_step_t(torch, seed: int, count: int, n_ops: int, device, ins_frac=(1, 2),
+                 erase_frac=(1, 4), salt: int = 0, absent_base: int = 1 << 31):
+    """One batch of mixed ops for a table whose inserted keys are the stream
+    positions [0, count) of `seed`: n_ops * ins_frac inserts, n_ops * erase_frac
+    erases, the rest finds.  Inserts take the next positions; erases and finds
+    each take half live keys (distinct positions of a random permutation of
+    [0, count), so no key is both updated and searched) and half absent keys
+    (positions from absent_base up, never inserted; erases and finds use
+    disjoint halves).  Returns (ops u8, keys i32, vals i32, new count, n_insert)
+    as tensors on `device`."""
     g = torch.Generator(device=device)
-    g.manual_seed((seed * 1000003 + count) & 0x7FFFFFFFFFFF)
-    n_ins = n_ops // 2
-    n_fd = n_ops // 4
-    n_er = n_ops - n_ins - n_fd
+    g.manual_seed((seed * 1000003 + count * 7919 + salt) & 0x7FFFFFFFFFFF)
+    n_ins = n_ops * ins_frac[0] // ins_frac[1]
+    n_er = n_ops * erase_frac[0] // erase_frac[1]
+    n_fd = n_ops - n_ins - n_er
     er_live = min(n_er // 2, count)
     fd_live = min(n_fd // 2, count - er_live)
-    perm = torch.randperm(count, generator=g, device=device)[: er_live + fd_live] if count else \
-        torch.zeros(0, dtype=torch.int64, device=device)
-    ins_pos = torch.arange(count, count + n_ins, device=device, dtype=torch.int64)
+    i64 = torch.int64
+    perm = (torch.randperm(count, generator=g, device=device)[: er_live + fd_live] if count
+            else torch.zeros(0, dtype=i64, device=device))
+    ins_pos = torch.arange(count, count + n_ins, device=device, dtype=i64)
     er_abs = n_er - er_live
     fd_abs = n_fd - fd_live
     quarter = 1 << 29
-    er_abs_pos = absent_base + torch.randperm(quarter, generator=g, device=device)[:er_abs] \
-        if er_abs else torch.zeros(0, dtype=torch.int64, device=device)
+    er_abs_pos = (absent_base + torch.randperm(quarter, generator=g, device=device)[:er_abs]
+                  if er_abs else torch.zeros(0, dtype=i64, device=device))
     fd_abs_pos = absent_base + quarter + torch.randint(0, quarter, (fd_abs,), generator=g,
                                                        device=device)
     pos = torch.cat([ins_pos, perm[:er_live], er_abs_pos, perm[er_live:], fd_abs_pos])
@@ -317,3 +320,17 @@ def multi_table_step(torch, seed: int, count: int, n_ops: int, device, absent_ba
     order = torch.randperm(ops.numel(), generator=g, device=device)
     to32 = lambda t: (t - ((t >> 31) << 32)).to(torch.int32)  # noqa: E731  two's complement view
     return ops[order], to32(keys[order]), to32(vals[order]), count + n_ins, n_ins
+
+
+def multi_table_step(torch, seed: int, count: int, n_ops: int, device, salt: int = 0):
+    """Mixed ops insert:find:erase = 2:1:1 (see mixed_step_t)."""
+    return mixed_step_t(torch, seed, count, n_ops, device, (1, 2), (1, 4), salt)
+
+
+def preload_t(torch, seed: int, n: int, device):
+    """The first n stream positions of `seed` as (keys i32, vals i32) tensors."""
+    pos = torch.arange(n, device=device, dtype=torch.int64)
+    keys = feistel_bits_t(pos, seed, 32)
+    vals = splitmix32_t(keys ^ (seed & MASK32))
+    to32 = lambda t: (t - ((t >> 31) << 32)).to(torch.int32)  # noqa: E731
+    return to32(keys), to32(vals)
