@@ -54,6 +54,8 @@ def parse_args():
                     help="inserts (and as many finds) in the CPU oracle sample")
     ap.add_argument("--no-tables", action="store_true", help="skip the multi-table leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-resize", action="store_true", help="skip the resize-stream leg")
+    ap.add_argument("--resize-batches", type=int, default=32)
     ap.add_argument("--tables-n", type=int, default=1024)
     ap.add_argument("--tables-steps", type=int, default=8)
     ap.add_argument("--serving-requests", type=int, default=3000)
@@ -247,11 +249,16 @@ def tables_leg(torch, H, dev, n_tables=1024, steps=8, seed=40):
     The same steps run once as one multi-table batch per step (CUDA graph
     replay) and once as one hive_execute per table per step, on two equal sets
     of tables; outputs must be identical."""
+    from paper_2510_15095_gb300 import autotune as AT
     from paper_2510_15095_gb300 import workload as W
     rng = np.random.default_rng(seed)
     caps = (np.exp(rng.uniform(10, 22, n_tables) * np.log(2)).astype(np.int64) // 32 + 1) * 32
     nops = np.exp(rng.uniform(6, 20, (steps, n_tables)) * np.log(2)).astype(np.int64)
-    K = 1024
+    # knobs from the autotuner for this class (resizable, 2^20 slots, 2:1:1)
+    tuned = AT.tune(1 << 20, 90, (2, 1, 1), True)
+    K = int(tuned.get("resize_batch", 1024))
+    knobs = {"max_evictions": int(tuned.get("max_evictions", 16)),
+             "placement": int(tuned.get("placement", 0))}
     ins_total = nops.sum(axis=0) // 2
     max_slots = caps + (ins_total * 10 // 9) + caps // 2 + 64 * K
     sets = []
@@ -259,7 +266,7 @@ def tables_leg(torch, H, dev, n_tables=1024, steps=8, seed=40):
         tabs = []
         for t in range(n_tables):
             tb = H.HiveTable(int(caps[t]), max_slots=int(max_slots[t]), resizable=True,
-                             resize_batch=K)
+                             resize_batch=K, **knobs)
             k, v = W.preload_t(torch, 7000 + t, int(caps[t]) // 2, dev)
             tb.insert(k, v, status=False)
             tabs.append(tb)
@@ -307,7 +314,81 @@ def tables_leg(torch, H, dev, n_tables=1024, steps=8, seed=40):
             "ops": ops_total, "batched_gops": ops_total / t_multi / 1e9,
             "plain_gops": ops_total / t_plain / 1e9, "speedup": t_plain / t_multi,
             "batched_s": t_multi, "plain_s": t_plain, "identical_results": bool(same),
-            "identical_capacity": bool(caps_same), "graph": True}
+            "identical_capacity": bool(caps_same), "graph": True,
+            "tuned": {"resize_batch": K, **knobs}}
+
+
+# ---------------------------------------------------------------------------
+# resize-stream leg: one table grows and shrinks through linear hashing
+# ---------------------------------------------------------------------------
+
+def resize_leg(torch, H, dev, batches=32, n_batch=1 << 22, seed=60):
+    """One resizable table starting with 2^20 live keys; `batches` growth
+    batches of 2^22 ops (insert:erase:find 40/20/40) then as many shrink
+    batches (20/40/40), finds Zipf(0.99) over live keys, thresholds 0.9/0.4,
+    K = 1024.  Also times single split and merge launches of 32,768 bucket
+    pairs (the size the paper reports resize throughput on)."""
+    from paper_2510_15095_gb300 import workload as W
+    start = 1 << 20
+    t = H.HiveTable(1 << 21, max_slots=1 << 27, resizable=True, resize_batch=1024, shrink=(2, 5))
+    k, v = W.preload_t(torch, seed, start, dev)
+    t.insert(k, v, status=False)
+    live = torch.arange(start, dtype=torch.int64, device=dev)
+    ctr = start
+    work = {"grow": [], "shrink": []}
+    for phase, fr in (("grow", ((2, 5), (1, 5))), ("shrink", ((1, 5), (2, 5)))):
+        for b in range(batches):
+            ops, keys, vals, live, ctr = W.stream_step_t(torch, seed, live, ctr, n_batch, dev,
+                                                         fr[0], fr[1], 0.99, salt=b)
+            work[phase].append((ops, keys, vals))
+        if phase == "grow":
+            peak = int(live.numel())
+    out = {}
+    t.profile(True)
+    t.profile_read()
+    for phase in ("grow", "shrink"):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for w in work[phase]:
+            t.execute(*w)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        out[f"{phase}_gops"] = batches * n_batch / dt / 1e9
+        out[f"{phase}_capacity_slots"] = t.capacity()
+    prof = t.profile_read()
+    t.profile(False)
+    st = t.stats()
+    size_end = t.size()
+    t.close()
+    # split / merge launches of 32,768 pairs on a table of 32,768 buckets
+    m = H.HiveTable(1 << 20, max_slots=1 << 22, resizable=True, resize_batch=32768, shrink=(2, 5))
+    k, v = W.preload_t(torch, seed + 1, (1 << 20) * 85 // 100, dev)
+    m.insert(k, v, status=False)
+    m.profile(True)
+    m.profile_read()
+    m.reserve(1 << 21)
+    sp = m.profile_read()
+    m.erase(k[: k.numel() * 45 // 100], status=False)
+    mg = m.profile_read()
+    m.profile(False)
+    m.close()
+    split_ms = sp.get("split", (float("nan"), 0))[0]
+    merge_ms = mg.get("merge", (float("nan"), 0))[0]
+    out.update({
+        "workload": (f"one resizable table from 2^20 live keys, {batches} growth + {batches} shrink "
+                     "batches of 2^22 ops (40/20/40 then 20/40/40 insert:erase:find, Zipf 0.99 "
+                     "finds), thresholds 0.9 / 0.4, K = 1024"),
+        "peak_live_keys": peak, "end_live_keys": size_end,
+        "splits": st["splits"], "merges": st["merges"],
+        "kernel_ms": {kk: vv[0] for kk, vv in prof.items()},
+        "split_32768_pairs_ms": split_ms, "merge_32768_pairs_ms": merge_ms,
+        "split_gbuckets_per_s": 32768 / (split_ms / 1e3) / 1e9,
+        # a split reads the source bucket and writes both buckets of the pair
+        "split_algorithmic_gbs": 32768 * 3 * 256 / (split_ms / 1e3) / 1e9,
+        "merge_gbuckets_per_s": 32768 / (merge_ms / 1e3) / 1e9,
+        "split_entries_per_s": (1 << 20) * 0.85 / (split_ms / 1e3),
+    })
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -458,8 +539,12 @@ def main():
     s_ins = t.stats()
     t.find(fk, vals_out=f_val, found=f_fnd)
     s_find = t.stats()
+    t.execute(mo, mk, mv)
+    s_mix = t.stats()
     probes_ins = s_ins["probes"]
     probes_find = s_find["probes"] - s_ins["probes"]
+    probes_mix = s_mix["probes"] - s_find["probes"]
+    claimed_mix = s_mix["claimed_fast"] - s_find["claimed_fast"]
     overflowed = s_ins["overflowed"]
     stashed = s_ins["stashed"]
 
@@ -495,18 +580,22 @@ def main():
     peak, peak_kind = measured_peak()
     ins_ms = prof.get("insert", (0.0, 1))
     find_ms = prof.get("find", (0.0, 1))
+    mix_ms = prof.get("mixed", (0.0, 1))
+    # mixed I/O: op, key, value in; value, status out
+    bytes_mix = 14 * n_mix + 256 * probes_mix + 32 * claimed_mix
     bytes_find = 9 * n_find + 256 * probes_find  # key in, value + flag out, probed buckets
     bytes_ins = 9 * n_ins + 256 * probes_ins + 32 * (n_ins - overflowed)  # + one written sector
     rl = {}
     for name, (tot, cnt), byts, kname in (("insert", ins_ms, bytes_ins, "k_ops<insert>"),
-                                            ("find", find_ms, bytes_find, "k_ops<find>")):
+                                            ("find", find_ms, bytes_find, "k_ops<find>"),
+                                            ("mixed", mix_ms, bytes_mix, "k_ops<mixed>")):
         avg = tot / max(cnt, 1)
         ach = byts / (avg / 1e3) / 1e9 if avg > 0 else 0.0
         traffic, _ = recorded_traffic(kname)
         rl[name] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": ach / peak, "traffic": traffic, "algorithmic_bytes": byts,
                     "avg_ms": avg, "kernel": kname, "peak_source": peak_kind}
-    dom = "insert" if ins_ms[0] >= find_ms[0] else "find"
+    dom = max(("insert", ins_ms[0]), ("find", find_ms[0]), ("mixed", mix_ms[0]), key=lambda x: x[1])[0]
     roofline = dict(rl[dom])
     roofline["others"] = {k: v for k, v in rl.items() if k != dom}
 
@@ -518,9 +607,12 @@ def main():
               "mixed_ms": float(ph[:, 2].mean()),
               "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
               "probes_per_find": probes_find / n_find, "probes_per_insert": probes_ins / n_ins,
+              "probes_per_mixed": probes_mix / n_mix,
               "insert_overflowed": overflowed, "insert_stashed": stashed}
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API with host buffers: the host-buffer
+    # calls stream pinned host arrays through device staging, overlapping the
+    # copies with the kernels; every copy is inside the timed region
     h_ik = torch.from_numpy(w["insert_keys"].view(np.int32)).pin_memory()
     h_iv = torch.from_numpy(w["insert_vals"].view(np.int32)).pin_memory()
     h_fk = torch.from_numpy(w["find_keys"].view(np.int32)).pin_memory()
@@ -532,35 +624,24 @@ def main():
     o_ff = torch.empty(n_find, dtype=torch.uint8).pin_memory()
     o_mv = torch.empty(n_mix, dtype=torch.int32).pin_memory()
     o_ms = torch.empty(n_mix, dtype=torch.uint8).pin_memory()
-    d_ik, d_iv, d_fk = torch.empty_like(ik), torch.empty_like(iv), torch.empty_like(fk)
-    d_mo, d_mk, d_mv = torch.empty_like(mo), torch.empty_like(mk), torch.empty_like(mv)
 
     def e2e_step():
         t.clear()
-        d_ik.copy_(h_ik, non_blocking=True)
-        d_iv.copy_(h_iv, non_blocking=True)
-        t.insert(d_ik, d_iv, status=ins_st)
-        o_st.copy_(ins_st, non_blocking=True)
-        d_fk.copy_(h_fk, non_blocking=True)
-        t.find(d_fk, vals_out=f_val, found=f_fnd)
-        o_fv.copy_(f_val, non_blocking=True)
-        o_ff.copy_(f_fnd, non_blocking=True)
-        d_mo.copy_(h_mo, non_blocking=True)
-        d_mk.copy_(h_mk, non_blocking=True)
-        d_mv.copy_(h_mv, non_blocking=True)
-        vo, st = t.execute(d_mo, d_mk, d_mv)
-        o_mv.copy_(vo, non_blocking=True)
-        o_ms.copy_(st, non_blocking=True)
+        t.insert_host(h_ik, h_iv, o_st)
+        t.find_host(h_fk, o_fv, o_ff)
+        t.execute_host(h_mo, h_mk, h_mv, o_mv, o_ms)
 
     e2e_step()
     torch.cuda.synchronize(dev)
     barrier()
+    w0 = time.perf_counter()
     e0.record(stream)
     for _ in range(args.e2e_steps):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1)
+    wall = time.perf_counter() - w0
+    e2e_ms = max(e0.elapsed_time(e1), 0.0)
     if world > 1:
         x = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(x, op=dist.ReduceOp.MAX)
@@ -568,7 +649,10 @@ def main():
     h2d = 4 * (2 * n_ins + n_find + 2 * n_mix) + n_mix
     d2h = n_ins + 5 * n_find + 5 * n_mix
     e2e = {"value": ops_step * args.e2e_steps * world / (e2e_ms / 1e3) / 1e9, "unit": "Gops/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+           "api": "hive_insert_host / hive_find_host / hive_execute_host (pinned host buffers)",
+           "host_wall_gops": ops_step * args.e2e_steps / wall / 1e9}
+    assert bool((o_st.numpy() == H.INSERTED).all()), "e2e insert statuses disagree"
     assert bool((o_ff.numpy() == w["is_hit"]).all()), "e2e find flags disagree"
 
     extra = {}
@@ -577,6 +661,8 @@ def main():
                                           steps=args.tables_steps)
     if not args.no_serving:
         extra["serving"] = serving_leg(torch, H, dev, n_requests=args.serving_requests)
+    if not args.no_resize:
+        extra["resize_stream"] = resize_leg(torch, H, dev, batches=args.resize_batches)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

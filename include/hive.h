@@ -94,7 +94,8 @@ typedef struct {
   uint32_t resizable;       /* 0: fixed capacity; 1: linear-hashing resize */
   uint32_t placement;       /* HIVE_PLACE_* */
   uint32_t lock_spin_limit; /* tries before a bucket-lock wait gives up */
-  uint32_t reserved0;       /* must be 0 */
+  uint32_t blocks_per_sm;   /* resident 256-thread blocks per SM of the bulk kernel's
+                               persistent grid; 0 = as many as fit (a tuning knob) */
 } hive_config;
 
 /* Per-table counters, accumulated since creation or the last hive_clear.
@@ -196,6 +197,13 @@ hive_status hive_execute(hive_table* t, const uint8_t* ops, const uint32_t* keys
 /* Live entries (buckets + stash).  Synchronises `stream`. */
 hive_status hive_size(hive_table* t, uint64_t* out, void* stream);
 
+/* Grows a resizable table until it has at least `slots` slots (or reaches
+ * max_slots), by linear-hashing splits in launches of K bucket pairs
+ * (Section IV-C1), so that later batches need not grow.  A fixed table only
+ * checks that it already has `slots` slots (else INVALID_ARG).  Stream-ordered;
+ * no synchronisation. */
+hive_status hive_reserve(hive_table* t, uint64_t slots, void* stream);
+
 /* Current slot capacity S * nBuckets (host-side state, no synchronisation). */
 hive_status hive_capacity(hive_table* t, uint64_t* slots_out);
 
@@ -222,6 +230,23 @@ hive_status hive_profile_enable(hive_table* t, int enable);
 /* Accumulates the recorded kernel times into *out (adding to what it holds)
  * and forgets them.  Synchronises on the recorded events. */
 hive_status hive_profile_read(hive_table* t, hive_profile_t* out);
+
+/* ---- Host-buffer calls ----
+ * Same operations with the op arrays in HOST memory.  The batch streams
+ * through device staging in chunks of 2^22 ops, two at a time, so that the
+ * host-to-device copy of one chunk, the kernels of the previous one and the
+ * copy back of the one before overlap (fully when the host buffers are pinned,
+ * e.g. cudaMallocHost).  Results equal the device-pointer calls (chunking does
+ * not change them under the batch contract).  The call returns when every
+ * output is in host memory.  The staging (about 120 MB) is allocated on the
+ * first host-buffer call of a table and freed by hive_destroy. */
+hive_status hive_insert_host(hive_table* t, const uint32_t* h_keys, const uint32_t* h_vals,
+                             uint64_t n, uint8_t* h_status, void* stream);
+hive_status hive_find_host(hive_table* t, const uint32_t* h_keys, uint64_t n,
+                           uint32_t* h_vals_out, uint8_t* h_found, void* stream);
+hive_status hive_execute_host(hive_table* t, const uint8_t* h_ops, const uint32_t* h_keys,
+                              const uint32_t* h_vals, uint64_t n, uint32_t* h_vals_out,
+                              uint8_t* h_status, void* stream);
 
 /* ---- Multi-table batches (many independent tables, one launch per phase) ----
  * Not in the paper: the tables are the paper's, the batching is a library

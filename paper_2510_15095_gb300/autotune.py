@@ -1,0 +1,144 @@
+"""Autotuner for the Hive table's runtime knobs.
+
+For a workload class -- capacity band, load band, op mix, fixed or resizable --
+it times every candidate configuration on a synthetic workload of that class
+on the current GPU and caches the fastest in a JSON file.  The knobs:
+
+* max_evictions (cuckoo displacement bound, Section III-B): 4, 8, 16, 32
+* placement (two-choice policy): balanced, BitHash1-first
+* blocks_per_sm (persistent grid of the bulk kernel): 2, 3, 4
+* resize_batch K (bucket pairs per split/merge launch, Section IV-C), for
+  resizable tables: 256, 1024, 4096
+
+The bucket width stays S = 32 (the paper's default; the kernels are built for
+two slots per lane of a 16-lane half-warp).  Every candidate must return the
+same per-op results -- the knobs change layout and speed only -- and the
+tuner checks that as it goes.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+import time
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "hive_gb300", "autotune.json")
+
+FIXED_SPACE = {"max_evictions": [4, 8, 16, 32], "placement": [0, 1], "blocks_per_sm": [2, 3, 4]}
+RESIZE_SPACE = {"resize_batch": [256, 1024, 4096], "max_evictions": [8, 16], "placement": [0, 1]}
+LOAD_BANDS = (50, 80, 90, 95)
+
+
+def workload_key(slots: int, load_pct: float, mix, resizable: bool) -> str:
+    """Class of a workload: log2 capacity band, nearest load band, op mix
+    normalised to tenths, fixed or resizable."""
+    cap = int(round(math.log2(max(int(slots), 32))))
+    band = min(LOAD_BANDS, key=lambda b: abs(b - load_pct))
+    tot = float(sum(mix))
+    m = ":".join(str(int(round(10 * x / tot))) for x in mix)
+    return f"cap{cap}-load{band}-mix{m}-{'resizable' if resizable else 'fixed'}"
+
+
+def load_cache(path: str | None = None) -> dict:
+    path = path or os.environ.get("HIVE_TUNE_CACHE", DEFAULT_CACHE)
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: str | None = None) -> str:
+    path = path or os.environ.get("HIVE_TUNE_CACHE", DEFAULT_CACHE)
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return path
+
+
+def candidates(space: dict):
+    names = sorted(space)
+    for vals in itertools.product(*(space[n] for n in names)):
+        yield dict(zip(names, vals))
+
+
+def _time_fixed(torch, H, W, slots, load_pct, mix, cfg, device, reps):
+    n_ins = int(slots * load_pct // 100)
+    keys, vals = W.preload_t(torch, 4242, n_ins, device)
+    tot = float(sum(mix))
+    # the mixed batch adds at most half of the free slots, so no insert can
+    # find the table full (FULL outcomes would depend on the layout)
+    ins_share = max(mix[0] / tot, 0.1)
+    n_mixed = max(64, int(slots * (100 - load_pct) / 100 * 0.5 / ins_share))
+    ops, mk, mv, _, _ = W.mixed_step_t(torch, 4242, n_ins, n_mixed, device,
+                                       (int(10 * mix[0] / tot), 10), (int(10 * mix[2] / tot), 10))
+    t = H.HiveTable(slots, **cfg)
+    best, out = float("inf"), None
+    for _ in range(reps):
+        t.clear()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        st = t.insert(keys, vals)
+        vo, ms = t.execute(ops, mk, mv)
+        torch.cuda.synchronize(device)
+        best = min(best, time.perf_counter() - t0)
+        out = (st, vo, ms)
+    t.close()
+    return (n_ins + n_mixed) / best / 1e9, out
+
+
+def _time_resizable(torch, H, W, slots, load_pct, mix, cfg, device, reps):
+    batches, n_b = 8, max(slots // 8, 64)
+    tot = float(sum(mix))
+    work, count = [], 0
+    for b in range(batches):
+        ops, mk, mv, count, _ = W.mixed_step_t(torch, 4343, count, n_b, device,
+                                               (int(10 * mix[0] / tot), 10),
+                                               (int(10 * mix[2] / tot), 10), salt=b)
+        work.append((ops, mk, mv))
+    best, out = float("inf"), None
+    for _ in range(reps):
+        t = H.HiveTable(max(slots // 64, 1024), max_slots=slots * 4, resizable=True, **cfg)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        res = [t.execute(*w) for w in work]
+        torch.cuda.synchronize(device)
+        best = min(best, time.perf_counter() - t0)
+        out = res
+        t.close()
+    return batches * n_b / best / 1e9, out
+
+
+def tune(slots: int, load_pct: float = 95, mix=(2, 1, 1), resizable: bool = False,
+         cache_path: str | None = None, reps: int = 2, space: dict | None = None,
+         device="cuda", force: bool = False) -> dict:
+    """Best configuration (HiveTable keyword arguments) for the workload class;
+    `mix` is insert:find:erase.  Results are cached under workload_key()."""
+    import torch
+
+    from . import hive as H
+    from . import workload as W
+
+    key = workload_key(slots, load_pct, mix, resizable)
+    cache = load_cache(cache_path)
+    if key in cache and not force:
+        return dict(cache[key]["config"])
+    space = space or (RESIZE_SPACE if resizable else FIXED_SPACE)
+    timer = _time_resizable if resizable else _time_fixed
+    results, ref = [], None
+    for cfg in candidates(space):
+        gops, out = timer(torch, H, W, slots, load_pct, mix, cfg, device, reps)
+        flat = [x for x in (out if resizable else [out]) for x in x]
+        if ref is None:
+            ref = flat
+        elif not all(torch.equal(a, b) for a, b in zip(ref, flat)):
+            raise RuntimeError(f"configuration {cfg} changed per-op results")
+        results.append({"config": cfg, "gops": gops})
+    results.sort(key=lambda r: -r["gops"])
+    cache[key] = {"config": results[0]["config"], "gops": results[0]["gops"],
+                  "candidates": results, "device": torch.cuda.get_device_name(device)}
+    save_cache(cache, cache_path)
+    return dict(results[0]["config"])

@@ -357,9 +357,9 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
       static_cast<uint64_t>(cfg->shrink_num) * cfg->grow_den >=
           static_cast<uint64_t>(cfg->grow_num) * cfg->shrink_den)
     return fail(HIVE_ERR_INVALID_ARG, "need 0 <= shrink < grow <= 1");
-  if (cfg->stash_permille > 1000 || cfg->placement > HIVE_PLACE_FIRST || cfg->reserved0 != 0 ||
+  if (cfg->stash_permille > 1000 || cfg->placement > HIVE_PLACE_FIRST || cfg->blocks_per_sm > 64 ||
       cfg->resizable > 1)
-    return fail(HIVE_ERR_INVALID_ARG, "bad stash_permille, placement, resizable or reserved0");
+    return fail(HIVE_ERR_INVALID_ARG, "bad stash_permille, placement, resizable or blocks_per_sm");
 
   hive_table* t = new (std::nothrow) hive_table();
   if (!t) return fail(HIVE_ERR_OOM, "host allocation failed");
@@ -387,6 +387,8 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
 
   cudaError_t e = cudaGetDevice(&t->device);
   if (e == cudaSuccess) e = query_occupancy(&t->L);
+  if (e == cudaSuccess && cfg->blocks_per_sm && static_cast<int>(cfg->blocks_per_sm) < t->L.ops_blocks_per_sm)
+    t->L.ops_blocks_per_sm = static_cast<int>(cfg->blocks_per_sm);
   if (e == cudaSuccess) e = cudaMalloc(&t->buckets, t->nb_max * kSlots * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->masks, t->nb_max * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->locks, t->nb_max * sizeof(uint32_t));
@@ -422,6 +424,7 @@ hive_status hive_destroy(hive_table* t) {
   cudaFree(t->ctrl);
   if (t->host_ctrl) cudaFreeHost(t->host_ctrl);
   free_lists(t);
+  free_staging(t);
   for (const auto& r : t->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -519,6 +522,29 @@ hive_status hive_size(hive_table* t, uint64_t* out, void* stream) {
   if (!out) return fail(HIVE_ERR_INVALID_ARG, "out must not be NULL");
   if ((st = readback(t, static_cast<cudaStream_t>(stream))) != HIVE_OK) return st;
   *out = t->host_ctrl->size;
+  return HIVE_OK;
+}
+
+hive_status hive_reserve(hive_table* t, uint64_t slots, void* stream) {
+  hive_status st = check_table(t);
+  if (st != HIVE_OK) return st;
+  if (!t->cfg.resizable) {
+    if (slots <= t->nb * kSlots) return HIVE_OK;
+    return fail(HIVE_ERR_INVALID_ARG, "a fixed-capacity table cannot grow");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bool any = false;
+  while (t->nb * kSlots < slots && t->nb < t->nb_max) {
+    bool did = false;
+    if ((st = split_step(t, s, &did)) != HIVE_OK) return st;
+    if (!did) break;
+    any = true;
+  }
+  if (any) {
+    // stash words may now fit a bucket
+    if ((st = mark_stash_dirty(t, s)) != HIVE_OK) return st;
+    HIVE_LAUNCH(t, HIVE_K_MAINT, s, launch_maintenance(make_view(t), s));
+  }
   return HIVE_OK;
 }
 

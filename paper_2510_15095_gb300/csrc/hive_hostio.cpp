@@ -1,0 +1,152 @@
+// Host-buffer calls: the op arrays live in host memory.  The batch is cut into
+// chunks that stream through two device staging slots: chunk i's inputs go up
+// on the copy-in stream while chunk i-1 runs on the caller's stream and chunk
+// i-2's results come down on the copy-out stream.  With pinned host buffers
+// the three overlap (the C2C link and the kernels work at once); pageable
+// buffers still work, the copies then block.  Chunking a batch does not change
+// its results under the batch contract.  Each call returns once every output
+// is in host memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+
+#include "hive.h"
+#include "hive_internal.h"
+
+using namespace hive;
+
+namespace {
+
+constexpr uint64_t kChunkOps = 1ull << 22;  // ops per chunk and staging slot
+
+hive_status hfail(hive_status s, const std::string& msg) {
+  set_last_error(msg);
+  return s;
+}
+
+hive_status hcuda(cudaError_t e, const char* what) {
+  set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? HIVE_ERR_OOM : HIVE_ERR_CUDA;
+}
+
+#define HCK(call)                                   \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return hcuda(e_, #call); \
+  } while (0)
+
+// Staging of one table, allocated on first use and kept until destroy.
+hive_status ensure_staging(hive_table* t) {
+  HostIO& io = t->io;
+  if (io.ready) return HIVE_OK;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaMalloc(&io.ops[k], kChunkOps);
+    if (e == cudaSuccess) e = cudaMalloc(&io.keys[k], kChunkOps * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&io.vals[k], kChunkOps * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&io.out[k], kChunkOps * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&io.st[k], kChunkOps);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io.in_ready[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io.done[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io.free[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&io.up, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&io.down, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    free_staging(t);
+    return hcuda(e, "allocating host-io staging");
+  }
+  io.ready = true;
+  return HIVE_OK;
+}
+
+enum Kind { kIns, kFind, kExec };
+
+hive_status run_host(hive_table* t, Kind kind, const uint8_t* h_ops, const uint32_t* h_keys,
+                     const uint32_t* h_vals, uint64_t n, uint32_t* h_out, uint8_t* h_st,
+                     cudaStream_t s) {
+  if (!t) return hfail(HIVE_ERR_INVALID_ARG, "table is NULL");
+  if (n >= (1ull << 32)) return hfail(HIVE_ERR_INVALID_ARG, "n must be below 2^32 per call");
+  if (n == 0) return HIVE_OK;
+  if (!h_keys || (kind == kIns && !h_vals) || (kind == kFind && !h_out) || (kind == kExec && !h_ops))
+    return hfail(HIVE_ERR_INVALID_ARG, "a required host array is NULL");
+  hive_status st = ensure_staging(t);
+  if (st != HIVE_OK) return st;
+  HostIO& io = t->io;
+  const uint64_t chunks = (n + kChunkOps - 1) / kChunkOps;
+  for (uint64_t c = 0; c < chunks; ++c) {
+    const int k = static_cast<int>(c & 1);
+    const uint64_t off = c * kChunkOps;
+    const uint64_t m = std::min(kChunkOps, n - off);
+    // inputs: after the slot's previous results have been copied out
+    HCK(cudaStreamWaitEvent(io.up, io.free[k], 0));
+    if (kind == kExec) HCK(cudaMemcpyAsync(io.ops[k], h_ops + off, m, cudaMemcpyHostToDevice, io.up));
+    HCK(cudaMemcpyAsync(io.keys[k], h_keys + off, m * 4, cudaMemcpyHostToDevice, io.up));
+    if (h_vals && kind != kFind)
+      HCK(cudaMemcpyAsync(io.vals[k], h_vals + off, m * 4, cudaMemcpyHostToDevice, io.up));
+    HCK(cudaEventRecord(io.in_ready[k], io.up));
+    // the op itself, on the caller's stream
+    HCK(cudaStreamWaitEvent(s, io.in_ready[k], 0));
+    if (kind == kIns)
+      st = hive_insert(t, io.keys[k], io.vals[k], m, h_st ? io.st[k] : nullptr, s);
+    else if (kind == kFind)
+      st = hive_find(t, io.keys[k], m, io.out[k], h_st ? io.st[k] : nullptr, s);
+    else
+      st = hive_execute(t, io.ops[k], io.keys[k], h_vals ? io.vals[k] : nullptr, m,
+                        h_out ? io.out[k] : nullptr, h_st ? io.st[k] : nullptr, s);
+    if (st != HIVE_OK) return st;
+    HCK(cudaEventRecord(io.done[k], s));
+    // results
+    HCK(cudaStreamWaitEvent(io.down, io.done[k], 0));
+    if (h_out && kind != kIns)
+      HCK(cudaMemcpyAsync(h_out + off, io.out[k], m * 4, cudaMemcpyDeviceToHost, io.down));
+    if (h_st) HCK(cudaMemcpyAsync(h_st + off, io.st[k], m, cudaMemcpyDeviceToHost, io.down));
+    HCK(cudaEventRecord(io.free[k], io.down));
+  }
+  HCK(cudaStreamSynchronize(io.down));
+  return HIVE_OK;
+}
+
+}  // namespace
+
+void hive::free_staging(hive_table* t) {
+  HostIO& io = t->io;
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(io.ops[k]);
+    cudaFree(io.keys[k]);
+    cudaFree(io.vals[k]);
+    cudaFree(io.out[k]);
+    cudaFree(io.st[k]);
+    if (io.in_ready[k]) cudaEventDestroy(io.in_ready[k]);
+    if (io.done[k]) cudaEventDestroy(io.done[k]);
+    if (io.free[k]) cudaEventDestroy(io.free[k]);
+  }
+  if (io.up) cudaStreamDestroy(io.up);
+  if (io.down) cudaStreamDestroy(io.down);
+  io = HostIO{};
+}
+
+extern "C" {
+
+hive_status hive_insert_host(hive_table* t, const uint32_t* h_keys, const uint32_t* h_vals,
+                             uint64_t n, uint8_t* h_status, void* stream) {
+  return run_host(t, kIns, nullptr, h_keys, h_vals, n, nullptr, h_status,
+                  static_cast<cudaStream_t>(stream));
+}
+
+hive_status hive_find_host(hive_table* t, const uint32_t* h_keys, uint64_t n,
+                           uint32_t* h_vals_out, uint8_t* h_found, void* stream) {
+  return run_host(t, kFind, nullptr, h_keys, nullptr, n, h_vals_out, h_found,
+                  static_cast<cudaStream_t>(stream));
+}
+
+hive_status hive_execute_host(hive_table* t, const uint8_t* h_ops, const uint32_t* h_keys,
+                              const uint32_t* h_vals, uint64_t n, uint32_t* h_vals_out,
+                              uint8_t* h_status, void* stream) {
+  return run_host(t, kExec, h_ops, h_keys, h_vals, n, h_vals_out, h_status,
+                  static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

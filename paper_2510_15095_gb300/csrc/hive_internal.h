@@ -150,6 +150,20 @@ cudaError_t query_occupancy(Launch* L);
 
 }  // namespace hive
 
+// Device staging of the host-buffer calls (hive_*_host), two slots.
+struct HostIO {
+  bool ready = false;
+  uint8_t* ops[2] = {nullptr, nullptr};
+  uint32_t* keys[2] = {nullptr, nullptr};
+  uint32_t* vals[2] = {nullptr, nullptr};
+  uint32_t* out[2] = {nullptr, nullptr};
+  uint8_t* st[2] = {nullptr, nullptr};
+  cudaEvent_t in_ready[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  cudaEvent_t free[2] = {nullptr, nullptr};
+  cudaStream_t up = nullptr, down = nullptr;
+};
+
 // The table object behind the opaque handle of include/hive.h.
 struct hive_table {
   hive_config cfg;
@@ -182,6 +196,7 @@ struct hive_table {
   bool prof = false;
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> ev_pool;
+  HostIO io;  // host-buffer call staging (allocated on first use)
 };
 
 // Helpers shared by the translation units of the library (hive_host.cpp
@@ -201,6 +216,7 @@ bool under_shrink(const hive_table* t, uint64_t live, uint64_t nb);
 // Contraction loop after a batch (Section IV-C2); reads counters back.
 hive_status contract_table(hive_table* t, cudaStream_t s);
 hive_status mark_stash_dirty(hive_table* t, cudaStream_t s);
+void free_staging(hive_table* t);  // releases the host-buffer call staging
 bool table_view(const hive_table* t, View* v, Launch* L, bool* resizable);
 void set_last_error(const std::string& msg);  // text returned by hive_last_error()
 }  // namespace hive

@@ -321,6 +321,90 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
   }
 }
 
+// Insert batches probe both candidate buckets of an op in one round: in load
+// u of group g, half-warp 0 reads the BitHash1 bucket and half-warp 1 the
+// BitHash2 bucket of op 4g + u.  An insert of a new key needs both buckets
+// anyway (step 1 must rule the key out of both before step 2 claims), so this
+// halves the dependent probe rounds of the find-shaped probe() above.  On a
+// match the home lane replaces the value with one CAS (Algorithm 1);
+// otherwise it records each bucket's free count and first free slot.
+__device__ __forceinline__ void probe_pair(const View& v, unsigned need, uint32_t b1,
+                                           uint32_t b2, uint32_t key, uint32_t val, int lane,
+                                           bool& done, uint8_t& st, uint32_t& f1, uint32_t& s1,
+                                           uint32_t& f2, uint32_t& s2, LaneCounters& cnt) {
+  const int h = lane >> 4;
+  const int hl = lane & 15;
+  const int my_g = lane >> 2, my_u = lane & 3;
+#pragma unroll 1
+  for (int g = 0; g < 8; ++g) {
+    const unsigned gneed = (need >> (4 * g)) & 0xFu;
+    if (!gneed) continue;
+    uint64_t wa[4], wb[4];
+    uint32_t kq[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int src = 4 * g + u;
+      const uint32_t q1 = __shfl_sync(kFull, b1, src);
+      const uint32_t q2 = __shfl_sync(kFull, b2, src);
+      kq[u] = __shfl_sync(kFull, key, src);
+      if ((gneed >> u) & 1u) {
+        const uint64_t* p = v.buckets + static_cast<uint64_t>(h ? q2 : q1) * kSlots + 2 * hl;
+        ld_frag(p, wa[u], wb[u]);
+      } else {
+        wa[u] = kEmptyWord;
+        wb[u] = kEmptyWord;
+      }
+    }
+    unsigned my_m = 0, my_mh = 0, my_el = 0, my_eh = 0;
+    uint32_t got = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool lo = key_of(wa[u]) == kq[u];
+      const bool hi = key_of(wb[u]) == kq[u];
+      const unsigned m = __ballot_sync(kFull, lo || hi);
+      const unsigned mh = __ballot_sync(kFull, hi);
+      const unsigned el = __ballot_sync(kFull, wa[u] == kEmptyWord);
+      const unsigned eh = __ballot_sync(kFull, wb[u] == kEmptyWord);
+      const uint32_t cv = lo ? val_of(wa[u]) : val_of(wb[u]);
+      const uint32_t x = __shfl_sync(kFull, cv, m ? __ffs(m) - 1 : 0);
+      if (u == my_u) {
+        my_m = m;
+        my_mh = mh;
+        my_el = el;
+        my_eh = eh;
+        got = x;
+      }
+    }
+    if (my_g == g && ((gneed >> my_u) & 1u)) {
+      if (my_m) {
+        // the lowest matching lane: the BitHash1 half wins when both match
+        done = true;
+        st = ST_REPLACED;
+        const uint32_t w = __ffs(my_m) - 1;
+        const uint32_t slot = 2 * (w & 15) + ((my_mh >> w) & 1u);
+        const uint32_t b = w < 16 ? b1 : b2;
+        uint64_t* sp = v.buckets + static_cast<uint64_t>(b) * kSlots + slot;
+        const uint64_t cur = pack(key, got);
+        if (atomicCAS(ull(sp), cur, pack(key, val)) == cur)
+          cnt.replaced += 1;
+        else
+          cnt.contract = true;
+      } else {
+        const unsigned e0 = my_el & 0xFFFFu, o0 = my_eh & 0xFFFFu;
+        const unsigned e1 = my_el >> 16, o1 = my_eh >> 16;
+        f1 = __popc(e0) + __popc(o0);
+        f2 = __popc(e1) + __popc(o1);
+        const uint32_t a0 = e0 ? 2u * (__ffs(e0) - 1) : kSlots;
+        const uint32_t a1 = o0 ? 2u * (__ffs(o0) - 1) + 1u : kSlots;
+        const uint32_t c0 = e1 ? 2u * (__ffs(e1) - 1) : kSlots;
+        const uint32_t c1 = o1 ? 2u * (__ffs(o1) - 1) + 1u : kSlots;
+        s1 = a0 < a1 ? a0 : a1;
+        s2 = c0 < c1 ? c0 : c1;
+      }
+    }
+  }
+}
+
 // Op arrays of one batch, or of one segment of a multi-table batch.
 struct OpPtrs {
   const uint8_t* ops;
@@ -389,11 +473,16 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
   // Probe the BitHash1 bucket of every op, then the BitHash2 bucket of the
   // ops still unresolved (Section IV-B: WCME over the d = 2 candidates).
   unsigned need = __ballot_sync(kFull, !done);
-  cnt.probes += __popc(need);
-  if (need) probe<MODE>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt);
-  need = __ballot_sync(kFull, !done);
-  cnt.probes += __popc(need);
-  if (need) probe<MODE>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt);
+  if (MODE == kModeInsert) {
+    cnt.probes += 2 * __popc(need);
+    if (need) probe_pair(v, need, b1, b2, key, val, lane, done, st, f1, s1, f2, s2, cnt);
+  } else {
+    cnt.probes += __popc(need);
+    if (need) probe<MODE>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt);
+    need = __ballot_sync(kFull, !done);
+    cnt.probes += __popc(need);
+    if (need) probe<MODE>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt);
+  }
 
   // The stash (Section IV-A step 4) holds keys that found no bucket room.
   if (!done && stash_n) {

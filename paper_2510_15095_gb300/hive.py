@@ -31,7 +31,8 @@ EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", 
            "hive_erase", "hive_execute", "hive_size", "hive_capacity", "hive_clear", "hive_check",
            "hive_stats", "hive_dump", "hive_profile_enable", "hive_profile_read",
            "hive_insert_noalloc", "hive_multi_create", "hive_multi_execute",
-           "hive_multi_destroy", "hive_last_error"]
+           "hive_multi_destroy", "hive_insert_host", "hive_find_host", "hive_execute_host",
+           "hive_reserve", "hive_last_error"]
 KERNEL_KINDS = ["find", "insert", "erase", "mixed", "evict", "maint", "split", "merge", "count"]
 
 
@@ -48,7 +49,7 @@ class Config(C.Structure):
                 ("grow_num", C.c_uint32), ("grow_den", C.c_uint32),
                 ("shrink_num", C.c_uint32), ("shrink_den", C.c_uint32),
                 ("resizable", C.c_uint32), ("placement", C.c_uint32),
-                ("lock_spin_limit", C.c_uint32), ("reserved0", C.c_uint32)]
+                ("lock_spin_limit", C.c_uint32), ("blocks_per_sm", C.c_uint32)]
 
 
 class Stats(C.Structure):
@@ -101,11 +102,15 @@ def load_library(path: str = LIB_PATH):
         L.hive_execute.argtypes = [vp, vp, vp, vp, u64, vp, vp, vp]
         L.hive_size.argtypes = [vp, C.POINTER(u64), vp]
         L.hive_capacity.argtypes = [vp, C.POINTER(u64)]
+        L.hive_reserve.argtypes = [vp, u64, vp]
         L.hive_clear.argtypes = [vp, vp]
         L.hive_check.argtypes = [vp, vp]
         L.hive_stats.argtypes = [vp, C.POINTER(Stats), vp]
         L.hive_dump.argtypes = [vp, C.POINTER(Image), vp]
         L.hive_insert_noalloc.argtypes = [vp, vp, vp, u64, vp, vp]
+        L.hive_insert_host.argtypes = [vp, vp, vp, u64, vp, vp]
+        L.hive_find_host.argtypes = [vp, vp, u64, vp, vp, vp]
+        L.hive_execute_host.argtypes = [vp, vp, vp, vp, u64, vp, vp, vp]
         L.hive_multi_create.argtypes = [C.POINTER(vp), C.c_uint32, C.c_uint32, u64, i32, vp,
                                         C.POINTER(vp)]
         L.hive_multi_execute.argtypes = [vp, C.POINTER(Segment), C.c_uint32, vp]
@@ -160,7 +165,7 @@ class HiveTable:
                  resizable: bool = False, max_evictions: int = 16, resize_batch: int = 1024,
                  stash_permille: int = 10, grow=(9, 10), shrink=(2, 5),
                  placement: int = PLACE_BALANCED, lock_spin_limit: int | None = None,
-                 stream=None):
+                 blocks_per_sm: int = 0, stream=None):
         self._L = load_library()
         cfg = Config()
         self._L.hive_config_default(C.byref(cfg))
@@ -175,6 +180,7 @@ class HiveTable:
         cfg.placement = int(placement)
         if lock_spin_limit is not None:
             cfg.lock_spin_limit = int(lock_spin_limit)
+        cfg.blocks_per_sm = int(blocks_per_sm)
         self.config = cfg
         h = C.c_void_p()
         _raise(self._L, self._L.hive_create(C.byref(cfg), _stream_ptr(stream), C.byref(h)))
@@ -268,11 +274,47 @@ class HiveTable:
             _dptr(vo, 4, n, "vals_out"), _dptr(st, 1, n, "status"), _stream_ptr(stream)))
         return vo, st
 
+    # -- host-buffer calls (pinned CPU tensors for overlap) ----------------
+    @staticmethod
+    def _hptr(t, itemsize, n, name):
+        if t is None:
+            return None
+        if t.is_cuda or not t.is_contiguous() or t.element_size() != itemsize or t.numel() < n:
+            raise ValueError(f"{name} must be a contiguous CPU tensor of {n} {itemsize}-byte items")
+        return t.data_ptr()
+
+    def insert_host(self, keys, vals, status=None, stream=None):
+        """hive_insert_host: keys/vals (and status, if given) are CPU tensors."""
+        n = keys.numel()
+        _raise(self._L, self._L.hive_insert_host(
+            self._h, self._hptr(keys, 4, n, "keys"), self._hptr(vals, 4, n, "vals"), n,
+            self._hptr(status, 1, n, "status"), _stream_ptr(stream)))
+        return status
+
+    def find_host(self, keys, vals_out, found=None, stream=None):
+        n = keys.numel()
+        _raise(self._L, self._L.hive_find_host(
+            self._h, self._hptr(keys, 4, n, "keys"), n, self._hptr(vals_out, 4, n, "vals_out"),
+            self._hptr(found, 1, n, "found"), _stream_ptr(stream)))
+        return vals_out, found
+
+    def execute_host(self, ops, keys, vals, vals_out=None, status=None, stream=None):
+        n = keys.numel()
+        _raise(self._L, self._L.hive_execute_host(
+            self._h, self._hptr(ops, 1, n, "ops"), self._hptr(keys, 4, n, "keys"),
+            self._hptr(vals, 4, n, "vals"), n, self._hptr(vals_out, 4, n, "vals_out"),
+            self._hptr(status, 1, n, "status"), _stream_ptr(stream)))
+        return vals_out, status
+
     # -- state ------------------------------------------------------------
     def size(self, stream=None) -> int:
         out = C.c_uint64()
         _raise(self._L, self._L.hive_size(self._h, C.byref(out), _stream_ptr(stream)))
         return int(out.value)
+
+    def reserve(self, slots: int, stream=None):
+        """Grow (resizable tables) to at least `slots` slots ahead of time."""
+        _raise(self._L, self._L.hive_reserve(self._h, int(slots), _stream_ptr(stream)))
 
     def capacity(self) -> int:
         out = C.c_uint64()

@@ -306,8 +306,10 @@ def mixed_step_t(torch, seed: int, count: int, n_ops: int, device, ins_frac=(1, 
     er_abs = n_er - er_live
     fd_abs = n_fd - fd_live
     quarter = 1 << 29
-    er_abs_pos = (absent_base + torch.randperm(quarter, generator=g, device=device)[:er_abs]
-                  if er_abs else torch.zeros(0, dtype=i64, device=device))
+    # distinct absent positions: consecutive from a random start (the Feistel
+    # bijection turns them into unrelated keys)
+    start = int(torch.randint(0, quarter, (1,), generator=g, device=device).item())
+    er_abs_pos = absent_base + (start + torch.arange(er_abs, device=device, dtype=i64)) % quarter
     fd_abs_pos = absent_base + quarter + torch.randint(0, quarter, (fd_abs,), generator=g,
                                                        device=device)
     pos = torch.cat([ins_pos, perm[:er_live], er_abs_pos, perm[er_live:], fd_abs_pos])
@@ -334,3 +336,92 @@ def preload_t(torch, seed: int, n: int, device):
     vals = splitmix32_t(keys ^ (seed & MASK32))
     to32 = lambda t: (t - ((t >> 31) << 32)).to(torch.int32)  # noqa: E731
     return to32(keys), to32(vals)
+
+
+def zipf_ranks_t(torch, n_items: int, s: float, count: int, generator, device):
+    """Zipf(s) ranks in [1, n_items] on torch tensors (rejection-inversion,
+    as zipf_ranks above)."""
+    f64 = torch.float64
+    one_m_s = 1.0 - s
+
+    def h(x):
+        return torch.exp(-s * torch.log(x))
+
+    def h_int(x):
+        lx = torch.log(x)
+        t = one_m_s * lx
+        safe = torch.where(t.abs() > 1e-8, t, torch.ones_like(t))
+        f = torch.where(t.abs() > 1e-8, torch.expm1(t) / safe, 1.0 + t / 2)
+        return f * lx
+
+    def h_int_inv(y):
+        t = y * one_m_s
+        safe = torch.where(t.abs() > 1e-8, t, torch.ones_like(t))
+        g = torch.where(t.abs() > 1e-8, torch.log1p(t) / safe, 1.0 - t / 2)
+        return torch.exp(g * y)
+
+    c = lambda v: torch.tensor(v, dtype=f64, device=device)  # noqa: E731
+    hx1 = float(h_int(c(1.5))) - 1.0
+    hn = float(h_int(c(n_items + 0.5)))
+    sq = 2.0 - float(h_int_inv(h_int(c(2.5)) - h(c(2.0))))
+    out = torch.empty(count, dtype=torch.int64, device=device)
+    todo = torch.arange(count, device=device)
+    while todo.numel():
+        u = hn + torch.rand(todo.numel(), generator=generator, dtype=f64, device=device) * (hx1 - hn)
+        x = h_int_inv(u)
+        k = torch.clamp(torch.floor(x + 0.5), 1, n_items)
+        acc = (k - x <= sq) | (u >= h_int(k + 0.5) - h(k))
+        out[todo[acc]] = k[acc].to(torch.int64)
+        todo = todo[~acc]
+    return out
+
+
+def stream_step_t(torch, seed: int, live_pos, counter: int, n_ops: int, device,
+                  ins_frac=(2, 5), erase_frac=(1, 5), zipf_s: float | None = 0.99, salt: int = 0):
+    """One batch of the resize stream: `live_pos` (int64 tensor) holds the
+    stream positions of the live keys, `counter` the next unused position.
+    Inserts take new positions; erases take distinct live keys; finds take live
+    keys that this batch does not erase, Zipf(zipf_s)-distributed over a seeded
+    permutation of the live set (uniform when zipf_s is None).  Returns (ops,
+    keys, vals, new live_pos, new counter)."""
+    g = torch.Generator(device=device)
+    g.manual_seed((seed * 1000003 + counter * 7919 + salt) & 0x7FFFFFFFFFFF)
+    nl = int(live_pos.numel())
+    n_ins = n_ops * ins_frac[0] // ins_frac[1]
+    n_er = min(n_ops * erase_frac[0] // erase_frac[1], nl)
+    n_fd = n_ops - n_ins - n_er
+    perm = torch.randperm(nl, generator=g, device=device)
+    er_idx = perm[:n_er]
+    keep = torch.ones(nl, dtype=torch.bool, device=device)
+    keep[er_idx] = False
+    kept = live_pos[keep]
+    nk = int(kept.numel())
+    if n_fd and nk:
+        if zipf_s is None:
+            fidx = torch.randint(0, nk, (n_fd,), generator=g, device=device)
+        else:
+            r = zipf_ranks_t(torch, nk, zipf_s, n_fd, g, device) - 1
+            bits = max(2, int(nk - 1).bit_length())
+            bits += bits & 1
+            y = feistel_bits_t(r, seed ^ 0x5A5A, bits)
+            bad = y >= nk
+            while bool(bad.any()):
+                y[bad] = feistel_bits_t(y[bad], seed ^ 0x5A5A, bits)
+                bad = y >= nk
+            fidx = y
+        fd_pos = kept[fidx]
+    else:
+        n_fd = 0
+        fd_pos = torch.zeros(0, dtype=torch.int64, device=device)
+    ins_pos = torch.arange(counter, counter + n_ins, device=device, dtype=torch.int64)
+    pos = torch.cat([ins_pos, live_pos[er_idx], fd_pos])
+    ops = torch.cat([torch.full((n_ins,), OP_INSERT, dtype=torch.uint8, device=device),
+                     torch.full((n_er,), OP_ERASE, dtype=torch.uint8, device=device),
+                     torch.full((n_fd,), OP_FIND, dtype=torch.uint8, device=device)])
+    keys = feistel_bits_t(pos, seed, 32)
+    vals = splitmix32_t(keys ^ (seed & MASK32))
+    vals = torch.where(ops == OP_INSERT, vals, torch.zeros_like(vals))
+    order = torch.randperm(ops.numel(), generator=g, device=device)
+    to32 = lambda t: (t - ((t >> 31) << 32)).to(torch.int32)  # noqa: E731
+    new_live = torch.cat([kept, ins_pos])
+    return ops[order], to32(keys[order]), to32(vals[order]), new_live, counter + n_ins

@@ -268,3 +268,40 @@ def test_2e26_slots_95pct_load(H):
     check_image(t, d)
     assert t.check() == 0
     t.close()
+
+
+def test_host_buffer_calls_match_device_calls(H):
+    """hive_*_host stream pinned host arrays through device staging in chunks
+    of 2^22 ops; with 5 million ops (two full slots and a ragged tail) the
+    results must equal the device-pointer calls bit for bit."""
+    n = 5_000_000
+    keys, c = W.take_keys(41, 0, n)
+    vals = W.values_for(keys, 41)
+    absent, _ = W.take_keys(41, c, n // 2)
+    q = np.concatenate([keys[::2], absent])
+    a = H.HiveTable(1 << 23)
+    b = H.HiveTable(1 << 23)
+    st_a = a.insert(up(H, keys), up(H, vals)).cpu()
+    hk = torch.from_numpy(keys.view(np.int32)).pin_memory()
+    hv = torch.from_numpy(vals.view(np.int32)).pin_memory()
+    st_b = torch.empty(n, dtype=torch.uint8).pin_memory()
+    b.insert_host(hk, hv, st_b)
+    assert torch.equal(st_a, st_b)
+    va, fa = a.find(up(H, q))
+    hq = torch.from_numpy(q.view(np.int32)).pin_memory()
+    vb = torch.empty(q.size, dtype=torch.int32).pin_memory()
+    fb = torch.empty(q.size, dtype=torch.uint8).pin_memory()
+    b.find_host(hq, vb, fb)
+    assert torch.equal(va.cpu(), vb) and torch.equal(fa.cpu(), fb)
+    rng = np.random.default_rng(4)
+    new, _ = W.take_keys(41, c + n, 100_000)
+    ops, mk, mv = W.mixed_batch(rng, keys, new, 100_000, 100_000, 300_000, seed=41)
+    vo_a, st_a = a.execute(torch.from_numpy(ops).cuda(), up(H, mk), up(H, mv))
+    vo_b = torch.empty(ops.size, dtype=torch.int32)
+    st_b = torch.empty(ops.size, dtype=torch.uint8)  # pageable buffers work too
+    b.execute_host(torch.from_numpy(ops), torch.from_numpy(mk.view(np.int32)),
+                   torch.from_numpy(mv.view(np.int32)), vo_b, st_b)
+    assert torch.equal(vo_a.cpu(), vo_b) and torch.equal(st_a.cpu(), st_b)
+    assert a.size() == b.size()
+    a.close()
+    b.close()
