@@ -169,13 +169,34 @@ hive_status split_step(hive_table* t, cudaStream_t s, bool* did) {
 
 // Before a batch with up to n_ins new keys.
 hive_status grow_for(hive_table* t, uint64_t n_ins, cudaStream_t s) {
-  bool any = false;
+  // K-pair steps of one round touch disjoint buckets and are fused into one
+  // launch; the policy still advances K pairs at a time.
+  bool any = false, have = false;
+  SplitPlan acc{};
   while (over_grow(t, t->size_host + n_ins, t->nb) && t->nb < t->nb_max) {
-    bool did = false;
-    hive_status st = split_step(t, s, &did);
-    if (st != HIVE_OK) return st;
-    if (!did) break;
+    SplitPlan pl{};
+    if (!plan_split(t, &pl)) break;
     any = true;
+    if (have && pl.half == acc.half && pl.src0 == acc.src0 + acc.count) {
+      acc.count += pl.count;
+      acc.M = pl.M;
+      acc.p = pl.p;
+      continue;
+    }
+    if (have) {
+      View v = make_view(t);
+      v.M = acc.M;
+      v.p = acc.p;
+      HIVE_LAUNCH(t, HIVE_K_SPLIT, s, launch_split(v, acc.src0, acc.count, acc.half, s));
+    }
+    acc = pl;
+    have = true;
+  }
+  if (have) {
+    View v = make_view(t);
+    v.M = acc.M;
+    v.p = acc.p;
+    HIVE_LAUNCH(t, HIVE_K_SPLIT, s, launch_split(v, acc.src0, acc.count, acc.half, s));
   }
   if (any && t->host_ctrl->stash_n) return mark_stash_dirty(t, s);
   return HIVE_OK;
@@ -238,9 +259,15 @@ hive_status hive::mark_stash_dirty(hive_table* t, cudaStream_t s) {
 }
 
 hive_status hive::contract_table(hive_table* t, cudaStream_t s) {
+  // Contraction (Section IV-C2), planned on the host from the size alone.
+  // The K-pair steps of one round form a wave: one pre-check of the words that
+  // cannot stay in their low bucket, one merge launch, one eviction launch for
+  // those words.  Merging moves words and loses none, so the size -- and with
+  // it the policy -- needs no read-back between waves.
   hive_status st = HIVE_OK;
-  // Contraction (Section IV-C2).
   t->merge_deferred = false;
+  bool merged = false;
+  uint64_t max_wave = ~0ull;
   while (t->nb > t->nb_init && under_shrink(t, t->size_host, t->nb)) {
     uint32_t M = t->M, p = t->p;
     if (p == 0) {
@@ -248,32 +275,48 @@ hive_status hive::contract_table(hive_table* t, cudaStream_t s) {
       M >>= 1;
       p = M + 1u;
     }
-    const uint64_t step =
-        std::min<uint64_t>({t->cfg.resize_batch, p, t->nb - t->nb_init});
-    if (step == 0 || over_grow(t, t->size_host, t->nb - step)) break;
+    const uint32_t p_start = p;
+    uint64_t nb = t->nb;
+    while (nb > t->nb_init && under_shrink(t, t->size_host, nb) && p_start - p < max_wave) {
+      const uint64_t step = std::min<uint64_t>({t->cfg.resize_batch, p, nb - t->nb_init});
+      if (step == 0 || over_grow(t, t->size_host, nb - step)) break;
+      p -= static_cast<uint32_t>(step);
+      nb -= step;
+      if (p == 0) break;  // the next step regresses the round: next wave
+    }
+    const uint32_t count = p_start - p;
+    if (count == 0) break;
     hive_table trial = *t;
     trial.M = M;
-    trial.p = p - static_cast<uint32_t>(step);
-    trial.nb = t->nb - step;
+    trial.p = p;
+    trial.nb = nb;
     const View vn = make_view(&trial);
     HIVE_CK(cudaMemsetAsync(&t->ctrl->merge_excess, 0, sizeof(unsigned), s));
-    HIVE_LAUNCH(t, HIVE_K_MERGE, s, launch_merge_excess(vn, static_cast<uint32_t>(step), s));
+    HIVE_LAUNCH(t, HIVE_K_MERGE, s, launch_merge_excess(vn, count, s));
     st = readback(t, s);
     if (st != HIVE_OK) return st;
     const uint64_t free_stash = t->stash_cap - t->host_ctrl->stash_claims;
     if (t->host_ctrl->merge_excess > free_stash) {
+      if (count > t->cfg.resize_batch) {
+        max_wave = t->cfg.resize_batch;  // retry this round one K-step at a time
+        continue;
+      }
       t->merge_deferred = true;
       break;
     }
-    st = ensure_lists(t, step * kSlots);
+    st = ensure_lists(t, static_cast<uint64_t>(count) * kSlots);
     if (st != HIVE_OK) return st;
-    HIVE_LAUNCH(t, HIVE_K_MERGE, s, launch_merge(vn, static_cast<uint32_t>(step), list_a(t), s));
+    HIVE_CK(cudaMemsetAsync(&t->ctrl->ovf_n, 0, sizeof(unsigned), s));
+    HIVE_LAUNCH(t, HIVE_K_MERGE, s, launch_merge(vn, count, list_a(t), s));
     t->M = trial.M;
     t->p = trial.p;
     t->nb = trial.nb;
-    t->merges += step;
+    t->merges += count;
     HIVE_LAUNCH(t, HIVE_K_EVICT, s,
                 launch_overflow(make_view(t), list_a(t), list_b(t), 0, nullptr, t->L, s));
+    merged = true;
+  }
+  if (merged) {
     HIVE_LAUNCH(t, HIVE_K_MAINT, s, launch_maintenance(make_view(t), s));
     st = readback(t, s);
     if (st != HIVE_OK) return st;
