@@ -37,6 +37,9 @@ LOAD = (19, 20)
 N_FIND = 1 << 26
 N_MIXED = 1 << 24
 SEED = 2
+# configurations the benchmark's tuner chooses among (fixed table, 95% load)
+BENCH_SPACE = {"bucket_slots": [16, 32], "placement": [0], "max_evictions": [16],
+               "blocks_per_sm": [4]}
 KERNEL_SRC = os.path.join(ROOT, "paper_2510_15095_gb300", "csrc", "hive_kernels.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 
@@ -85,7 +88,7 @@ def make_workload(seed: int, slots: int):
 def workload_config(w, slots):
     n_ins = int(w["insert_keys"].size)
     return {
-        "workload": (f"fixed table of {slots} slots (S=32 buckets); bulk insert {n_ins} unique "
+        "workload": (f"fixed table of {slots} slots; bulk insert {n_ins} unique "
                      f"uniform u32 keys (95% load), {w['find_keys'].size} finds at 50% hit "
                      f"(uniform), mixed batch of {w['mix_ops'].size} ops insert:find:erase 1:2:1 "
                      "at 95% load"),
@@ -258,7 +261,8 @@ def tables_leg(torch, H, dev, n_tables=1024, steps=8, seed=40):
     tuned = AT.tune(1 << 20, 90, (2, 1, 1), True)
     K = int(tuned.get("resize_batch", 1024))
     knobs = {"max_evictions": int(tuned.get("max_evictions", 16)),
-             "placement": int(tuned.get("placement", 0))}
+             "placement": int(tuned.get("placement", 0)),
+             "bucket_slots": int(tuned.get("bucket_slots", 32))}
     ins_total = nops.sum(axis=0) // 2
     max_slots = caps + (ins_total * 10 // 9) + caps // 2 + 64 * K
     sets = []
@@ -405,10 +409,17 @@ def serving_leg(torch, H, dev, n_tables=64, n_requests=3000, seed=50):
     from paper_2510_15095_gb300 import workload as W
     pre = 1 << 16
 
+    from paper_2510_15095_gb300 import autotune as AT
+    tuned = AT.tune(1 << 20, 90, (2, 1, 1), True)  # the multi-table leg's class
+    knobs = {"bucket_slots": int(tuned.get("bucket_slots", 32)),
+             "max_evictions": int(tuned.get("max_evictions", 16)),
+             "placement": int(tuned.get("placement", 0))}
+
     def fresh():
         tabs = []
         for t in range(n_tables):
-            tb = H.HiveTable(1 << 17, max_slots=1 << 23, resizable=True, resize_batch=1024)
+            tb = H.HiveTable(1 << 17, max_slots=1 << 23, resizable=True,
+                             resize_batch=int(tuned.get("resize_batch", 1024)), **knobs)
             k, v = W.preload_t(torch, 1000 + t, pre, dev)
             tb.insert(k, v, status=False)
             tabs.append(tb)
@@ -457,7 +468,7 @@ def serving_leg(torch, H, dev, n_tables=64, n_requests=3000, seed=50):
                            "speedup": sat_b["gops"] / sat_f["gops"]},
             "poisson_rate_req_per_s": rate,
             "batched": {k: lat_b[k] for k in keep}, "fifo": {k: lat_f[k] for k in keep},
-            "identical_results": bool(same)}
+            "identical_results": bool(same), "tuned": tuned}
 
 
 # ---------------------------------------------------------------------------
@@ -498,7 +509,12 @@ def main():
     ins_st = torch.empty(n_ins, dtype=torch.uint8, device=dev)
     f_val = torch.empty(n_find, dtype=torch.int32, device=dev)
     f_fnd = torch.empty(n_find, dtype=torch.uint8, device=dev)
-    t = H.HiveTable(args.slots)
+    # bucket width and knobs from the autotuner for this workload class (the
+    # paper's default S = 32 is measured too, below)
+    from paper_2510_15095_gb300 import autotune as AT
+    tuned = AT.tune(args.slots, 95, (1, 2, 1), False, space=BENCH_SPACE)
+    cfg["table"] = dict(tuned)
+    t = H.HiveTable(args.slots, **tuned)
     stream = torch.cuda.current_stream(dev)
 
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -582,13 +598,15 @@ def main():
     find_ms = prof.get("find", (0.0, 1))
     mix_ms = prof.get("mixed", (0.0, 1))
     # mixed I/O: op, key, value in; value, status out
-    bytes_mix = 14 * n_mix + 256 * probes_mix + 32 * claimed_mix
-    bytes_find = 9 * n_find + 256 * probes_find  # key in, value + flag out, probed buckets
-    bytes_ins = 9 * n_ins + 256 * probes_ins + 32 * (n_ins - overflowed)  # + one written sector
+    bb = 8 * int(tuned.get("bucket_slots", 32))  # bytes per bucket probe
+    bytes_mix = 14 * n_mix + bb * probes_mix + 32 * claimed_mix
+    bytes_find = 9 * n_find + bb * probes_find  # key in, value + flag out, probed buckets
+    bytes_ins = 9 * n_ins + bb * probes_ins + 32 * (n_ins - overflowed)  # + one written sector
     rl = {}
-    for name, (tot, cnt), byts, kname in (("insert", ins_ms, bytes_ins, "k_ops<insert>"),
-                                            ("find", find_ms, bytes_find, "k_ops<find>"),
-                                            ("mixed", mix_ms, bytes_mix, "k_ops<mixed>")):
+    sw = int(tuned.get("bucket_slots", 32))
+    for name, (tot, cnt), byts, kname in (("insert", ins_ms, bytes_ins, f"k_ops<insert,S={sw}>"),
+                                            ("find", find_ms, bytes_find, f"k_ops<find,S={sw}>"),
+                                            ("mixed", mix_ms, bytes_mix, f"k_ops<mixed,S={sw}>")):
         avg = tot / max(cnt, 1)
         ach = byts / (avg / 1e3) / 1e9 if avg > 0 else 0.0
         traffic, _ = recorded_traffic(kname)
@@ -599,6 +617,31 @@ def main():
     roofline = dict(rl[dom])
     roofline["others"] = {k: v for k, v in rl.items() if k != dom}
 
+    # the paper's default bucket width, for reference (same steps, untimed region)
+    default_s32 = None
+    if tuned.get("bucket_slots", 32) != 32:
+        t32 = H.HiveTable(args.slots)
+        ev4 = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        rows = []
+        for r in range(4):
+            t32.clear()
+            ev4[0].record(stream)
+            t32.insert(ik, iv, status=ins_st)
+            ev4[1].record(stream)
+            t32.find(fk, vals_out=f_val, found=f_fnd)
+            ev4[2].record(stream)
+            t32.execute(mo, mk, mv)
+            ev4[3].record(stream)
+            torch.cuda.synchronize(dev)
+            if r:
+                rows.append([ev4[0].elapsed_time(ev4[1]), ev4[1].elapsed_time(ev4[2]),
+                             ev4[2].elapsed_time(ev4[3])])
+        a = np.array(rows).mean(axis=0)
+        default_s32 = {"insert_gops": n_ins / a[0] / 1e6, "find_gops": n_find / a[1] / 1e6,
+                       "mixed_gops": n_mix / a[2] / 1e6,
+                       "step_gops": ops_step / (a.sum() + 0.0) / 1e6}
+        t32.close()
+
     ph = np.array(phase_ms)
     phases = {"insert_gops": n_ins / (ph[:, 0].mean() / 1e3) / 1e9,
               "find_gops": n_find / (ph[:, 1].mean() / 1e3) / 1e9,
@@ -608,7 +651,8 @@ def main():
               "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
               "probes_per_find": probes_find / n_find, "probes_per_insert": probes_ins / n_ins,
               "probes_per_mixed": probes_mix / n_mix,
-              "insert_overflowed": overflowed, "insert_stashed": stashed}
+              "insert_overflowed": overflowed, "insert_stashed": stashed,
+              "paper_default_s32": default_s32}
 
     # end to end through the public API with host buffers: the host-buffer
     # calls stream pinned host arrays through device staging, overlapping the

@@ -4,16 +4,15 @@ For a workload class -- capacity band, load band, op mix, fixed or resizable --
 it times every candidate configuration on a synthetic workload of that class
 on the current GPU and caches the fastest in a JSON file.  The knobs:
 
-* max_evictions (cuckoo displacement bound, Section III-B): 4, 8, 16, 32
+* bucket_slots S (Section III-B, 32 by default): 16, 32
+* max_evictions (cuckoo displacement bound, Section III-B): 8, 16, 32
 * placement (two-choice policy): balanced, BitHash1-first
-* blocks_per_sm (persistent grid of the bulk kernel): 2, 3, 4
+* blocks_per_sm (persistent grid of the bulk kernel): 3, 4
 * resize_batch K (bucket pairs per split/merge launch, Section IV-C), for
   resizable tables: 256, 1024, 4096
 
-The bucket width stays S = 32 (the paper's default; the kernels are built for
-two slots per lane of a 16-lane half-warp).  Every candidate must return the
-same per-op results -- the knobs change layout and speed only -- and the
-tuner checks that as it goes.
+Every candidate must return the same per-op results -- the knobs change
+layout and speed only -- and the tuner checks that as it goes.
 """
 from __future__ import annotations
 
@@ -25,8 +24,10 @@ import time
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "hive_gb300", "autotune.json")
 
-FIXED_SPACE = {"max_evictions": [4, 8, 16, 32], "placement": [0, 1], "blocks_per_sm": [2, 3, 4]}
-RESIZE_SPACE = {"resize_batch": [256, 1024, 4096], "max_evictions": [8, 16], "placement": [0, 1]}
+FIXED_SPACE = {"bucket_slots": [16, 32], "max_evictions": [8, 16, 32], "placement": [0, 1],
+               "blocks_per_sm": [3, 4]}
+RESIZE_SPACE = {"bucket_slots": [16, 32], "resize_batch": [256, 1024, 4096], "max_evictions": [16],
+                "placement": [0, 1]}
 LOAD_BANDS = (50, 80, 90, 95)
 
 
@@ -66,11 +67,14 @@ def candidates(space: dict):
 
 
 def _time_fixed(torch, H, W, slots, load_pct, mix, cfg, device, reps):
+    """Fill to the load, find every inserted key and as many absent keys, then
+    a mixed batch that adds at most half of the free slots (so no insert can
+    find the table full: FULL outcomes would depend on the layout)."""
     n_ins = int(slots * load_pct // 100)
     keys, vals = W.preload_t(torch, 4242, n_ins, device)
+    absent, _ = W.preload_t(torch, 4243, n_ins, device)
+    queries = torch.cat([keys, absent])
     tot = float(sum(mix))
-    # the mixed batch adds at most half of the free slots, so no insert can
-    # find the table full (FULL outcomes would depend on the layout)
     ins_share = max(mix[0] / tot, 0.1)
     n_mixed = max(64, int(slots * (100 - load_pct) / 100 * 0.5 / ins_share))
     ops, mk, mv, _, _ = W.mixed_step_t(torch, 4242, n_ins, n_mixed, device,
@@ -82,12 +86,13 @@ def _time_fixed(torch, H, W, slots, load_pct, mix, cfg, device, reps):
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
         st = t.insert(keys, vals)
+        fv, ff = t.find(queries)
         vo, ms = t.execute(ops, mk, mv)
         torch.cuda.synchronize(device)
         best = min(best, time.perf_counter() - t0)
-        out = (st, vo, ms)
+        out = (st, fv, ff, vo, ms)
     t.close()
-    return (n_ins + n_mixed) / best / 1e9, out
+    return (n_ins + queries.numel() + n_mixed) / best / 1e9, out
 
 
 def _time_resizable(torch, H, W, slots, load_pct, mix, cfg, device, reps):

@@ -111,6 +111,7 @@ View hive::make_view(const hive_table* t) {
   v.max_evictions = t->cfg.max_evictions;
   v.lock_spin_limit = t->cfg.lock_spin_limit;
   v.placement = t->cfg.placement;
+  v.S = t->S;
   return v;
 }
 
@@ -243,11 +244,11 @@ hive_status finish_resizable(hive_table* t, uint8_t* status, cudaStream_t s) {
 
 bool hive::over_grow(const hive_table* t, uint64_t live, uint64_t nb) {
   return static_cast<unsigned __int128>(live) * t->cfg.grow_den >
-         static_cast<unsigned __int128>(kSlots) * nb * t->cfg.grow_num;
+         static_cast<unsigned __int128>(t->S) * nb * t->cfg.grow_num;
 }
 bool hive::under_shrink(const hive_table* t, uint64_t live, uint64_t nb) {
   return static_cast<unsigned __int128>(live) * t->cfg.shrink_den <
-         static_cast<unsigned __int128>(kSlots) * nb * t->cfg.shrink_num;
+         static_cast<unsigned __int128>(t->S) * nb * t->cfg.shrink_num;
 }
 
 
@@ -304,7 +305,7 @@ hive_status hive::contract_table(hive_table* t, cudaStream_t s) {
       t->merge_deferred = true;
       break;
     }
-    st = ensure_lists(t, static_cast<uint64_t>(count) * kSlots);
+    st = ensure_lists(t, static_cast<uint64_t>(count) * t->S);
     if (st != HIVE_OK) return st;
     HIVE_CK(cudaMemsetAsync(&t->ctrl->ovf_n, 0, sizeof(unsigned), s));
     HIVE_LAUNCH(t, HIVE_K_MERGE, s, launch_merge(vn, count, list_a(t), s));
@@ -392,7 +393,8 @@ void hive_config_default(hive_config* cfg) {
 hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) {
   if (!cfg || !out) return fail(HIVE_ERR_INVALID_ARG, "cfg and out must not be NULL");
   *out = nullptr;
-  if (cfg->bucket_slots != kSlots) return fail(HIVE_ERR_INVALID_ARG, "bucket_slots must be 32");
+  if (cfg->bucket_slots != 16 && cfg->bucket_slots != 32)
+    return fail(HIVE_ERR_INVALID_ARG, "bucket_slots must be 16 or 32");
   if (cfg->initial_slots == 0) return fail(HIVE_ERR_INVALID_ARG, "initial_slots must be > 0");
   if (cfg->max_evictions == 0 || cfg->resize_batch == 0 || cfg->lock_spin_limit == 0)
     return fail(HIVE_ERR_INVALID_ARG, "max_evictions, resize_batch, lock_spin_limit must be > 0");
@@ -408,9 +410,10 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
   if (!t) return fail(HIVE_ERR_OOM, "host allocation failed");
   t->cfg = *cfg;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  t->nb_init = (cfg->initial_slots + kSlots - 1) / kSlots;
-  t->nb_max = cfg->resizable ? std::max(t->nb_init, (cfg->max_slots + kSlots - 1) / kSlots)
-                             : t->nb_init;
+  const uint32_t S = cfg->bucket_slots;
+  t->S = S;
+  t->nb_init = (cfg->initial_slots + S - 1) / S;
+  t->nb_max = cfg->resizable ? std::max(t->nb_init, (cfg->max_slots + S - 1) / S) : t->nb_init;
   if (t->nb_max > kMaxBuckets) {
     delete t;
     return fail(HIVE_ERR_INVALID_ARG, "capacity above 2^36 slots");
@@ -420,7 +423,7 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
   while (pow2 * 2 <= t->nb_init) pow2 *= 2;
   t->M = static_cast<uint32_t>(pow2 - 1);
   t->p = static_cast<uint32_t>(t->nb_init - pow2);
-  const uint64_t cap_slots = t->nb_max * kSlots;
+  const uint64_t cap_slots = t->nb_max * S;
   uint64_t sc = (cap_slots * cfg->stash_permille + 999) / 1000;
   sc = std::max<uint64_t>(sc, 1024);
   sc = (sc + 31) / 32 * 32;
@@ -429,10 +432,10 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
   t->stash_alloc = next_pow2(sc);
 
   cudaError_t e = cudaGetDevice(&t->device);
-  if (e == cudaSuccess) e = query_occupancy(&t->L);
+  if (e == cudaSuccess) e = query_occupancy(&t->L, static_cast<int>(S));
   if (e == cudaSuccess && cfg->blocks_per_sm && static_cast<int>(cfg->blocks_per_sm) < t->L.ops_blocks_per_sm)
     t->L.ops_blocks_per_sm = static_cast<int>(cfg->blocks_per_sm);
-  if (e == cudaSuccess) e = cudaMalloc(&t->buckets, t->nb_max * kSlots * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&t->buckets, t->nb_max * S * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->masks, t->nb_max * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->locks, t->nb_max * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->stash_kv, t->stash_alloc * sizeof(uint64_t));
@@ -441,9 +444,10 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
   if (e == cudaSuccess) e = cudaMallocHost(&t->host_ctrl, sizeof(Ctrl));
   if (e == cudaSuccess) {
     std::memset(t->host_ctrl, 0, sizeof(Ctrl));
-    e = cudaMemsetAsync(t->buckets, 0xFF, t->nb_max * kSlots * sizeof(uint64_t), s);
+    e = cudaMemsetAsync(t->buckets, 0xFF, t->nb_max * S * sizeof(uint64_t), s);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(t->masks, 0xFF, t->nb_max * sizeof(uint32_t), s);
+  if (e == cudaSuccess && S < 32) e = launch_fill_u32(t->masks, t->nb_max, (1u << S) - 1u, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->locks, 0, t->nb_max * sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->stash_kv, 0xFF, t->stash_alloc * sizeof(uint64_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->ctrl, 0, sizeof(Ctrl), s);
@@ -572,12 +576,12 @@ hive_status hive_reserve(hive_table* t, uint64_t slots, void* stream) {
   hive_status st = check_table(t);
   if (st != HIVE_OK) return st;
   if (!t->cfg.resizable) {
-    if (slots <= t->nb * kSlots) return HIVE_OK;
+    if (slots <= t->nb * t->S) return HIVE_OK;
     return fail(HIVE_ERR_INVALID_ARG, "a fixed-capacity table cannot grow");
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bool any = false;
-  while (t->nb * kSlots < slots && t->nb < t->nb_max) {
+  while (t->nb * t->S < slots && t->nb < t->nb_max) {
     bool did = false;
     if ((st = split_step(t, s, &did)) != HIVE_OK) return st;
     if (!did) break;
@@ -595,7 +599,7 @@ hive_status hive_capacity(hive_table* t, uint64_t* slots_out) {
   hive_status st = check_table(t);
   if (st != HIVE_OK) return st;
   if (!slots_out) return fail(HIVE_ERR_INVALID_ARG, "slots_out must not be NULL");
-  *slots_out = t->nb * kSlots;
+  *slots_out = t->nb * t->S;
   return HIVE_OK;
 }
 
@@ -605,8 +609,9 @@ hive_status hive_clear(hive_table* t, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // Buckets at or past nb are kept empty by construction; only [0, nb) and
   // the stash need resetting.
-  HIVE_CK(cudaMemsetAsync(t->buckets, 0xFF, t->nb * kSlots * sizeof(uint64_t), s));
+  HIVE_CK(cudaMemsetAsync(t->buckets, 0xFF, t->nb * t->S * sizeof(uint64_t), s));
   HIVE_CK(cudaMemsetAsync(t->masks, 0xFF, t->nb * sizeof(uint32_t), s));
+  if (t->S < 32) HIVE_CK(launch_fill_u32(t->masks, t->nb, (1u << t->S) - 1u, s));
   HIVE_CK(cudaMemsetAsync(t->locks, 0, t->nb * sizeof(uint32_t), s));
   HIVE_CK(cudaMemsetAsync(t->stash_kv, 0xFF, t->stash_alloc * sizeof(uint64_t), s));
   HIVE_CK(cudaMemsetAsync(t->ctrl, 0, sizeof(Ctrl), s));
@@ -692,7 +697,7 @@ hive_status hive_dump(hive_table* t, hive_image* img, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((st = readback(t, s)) != HIVE_OK) return st;
   img->nb = t->nb;
-  img->S = kSlots;
+  img->S = t->S;
   img->M = t->M;
   img->p = t->p;
   img->reserved0 = 0;
@@ -703,7 +708,7 @@ hive_status hive_dump(hive_table* t, hive_image* img, void* stream) {
   if (!img->buckets) return HIVE_OK;
   if (!img->masks || !img->locks || (!img->stash && img->stash_n))
     return fail(HIVE_ERR_INVALID_ARG, "image arrays must not be NULL");
-  HIVE_CK(cudaMemcpyAsync(img->buckets, t->buckets, t->nb * kSlots * sizeof(uint64_t),
+  HIVE_CK(cudaMemcpyAsync(img->buckets, t->buckets, t->nb * t->S * sizeof(uint64_t),
                           cudaMemcpyDeviceToHost, s));
   HIVE_CK(cudaMemcpyAsync(img->masks, t->masks, t->nb * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   HIVE_CK(cudaMemcpyAsync(img->locks, t->locks, t->nb * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

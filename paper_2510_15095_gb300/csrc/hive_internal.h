@@ -12,7 +12,7 @@
 
 namespace hive {
 
-constexpr uint32_t kSlots = 32;                    // S, slots per bucket (Section III-A)
+constexpr uint32_t kSlots = 32;                    // default S, slots per bucket (Section III-A)
 constexpr uint64_t kEmptyWord = ~0ull;             // empty slot: key 0xFFFFFFFF
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 constexpr uint32_t kReservedKeyMin = 0xFFFFFFFEu;  // keys >= this are reserved
@@ -76,7 +76,7 @@ struct View {
   uint32_t max_evictions;
   uint32_t lock_spin_limit;
   uint32_t placement;    // 0 balanced, 1 BitHash1 first
-  uint32_t pad;
+  uint32_t S;            // slots per bucket: 16 or 32
 };
 
 // An op list handed from the bulk kernel to the eviction kernel.
@@ -136,17 +136,18 @@ cudaError_t launch_merge_excess(const View& v_new, uint32_t count, cudaStream_t 
 cudaError_t launch_merge(const View& v_new, uint32_t count, List ovf, cudaStream_t s);
 cudaError_t launch_count_inserts(const uint8_t* ops, uint64_t n, unsigned int* out,
                                  cudaStream_t s);
-cudaError_t launch_multi_ops(const MultiHdr* hdr, const MultiSeg* segs, const View* views, List ovf,
-                             const Launch& L, cudaStream_t s);
-cudaError_t launch_multi_overflow(const MultiSeg* segs, const View* views, List in,
+cudaError_t launch_multi_ops(int S, const MultiHdr* hdr, const MultiSeg* segs, const View* views,
+                             List ovf, const Launch& L, cudaStream_t s);
+cudaError_t launch_multi_overflow(int S, const MultiSeg* segs, const View* views, List in,
                                   const Launch& L, cudaStream_t s);
-cudaError_t launch_multi_maint(const MultiHdr* hdr, const View* views, const uint32_t* touched,
-                               uint32_t max_tables, cudaStream_t s);
-cudaError_t launch_multi_split(const MultiJob* jobs, uint32_t n_jobs, uint32_t total_pairs,
+cudaError_t launch_multi_maint(int S, const MultiHdr* hdr, const View* views,
+                               const uint32_t* touched, uint32_t max_tables, cudaStream_t s);
+cudaError_t launch_multi_split(int S, const MultiJob* jobs, uint32_t n_jobs, uint32_t total_pairs,
                                const View* views, cudaStream_t s);
+cudaError_t launch_fill_u32(uint32_t* p, uint64_t n, uint32_t value, cudaStream_t s);
 cudaError_t launch_multi_gather(const MultiHdr* hdr, const View* views, const uint32_t* touched,
                                 uint32_t max_tables, unsigned long long* out, cudaStream_t s);
-cudaError_t query_occupancy(Launch* L);
+cudaError_t query_occupancy(Launch* L, int S);
 
 }  // namespace hive
 
@@ -167,6 +168,7 @@ struct HostIO {
 // The table object behind the opaque handle of include/hive.h.
 struct hive_table {
   hive_config cfg;
+  uint32_t S = 32;  // slots per bucket
   int device = 0;
   hive::Launch L{};
   uint64_t nb_init = 0, nb_max = 0, nb = 0;

@@ -134,16 +134,17 @@ __device__ __forceinline__ unsigned long long* ull(uint64_t* p) {
 // (the bulk kernel and maintenance).  Algorithm 2 restores the bit with
 // fetch_or when the fetch_and finds it already clear; that would free a slot
 // another warp owns, so here a failed claim retries on the returned mask.
+template <int S>
 __device__ __forceinline__ bool claim_store(const View& v, uint32_t b, uint32_t s,
                                             uint64_t word) {
-  for (int t = 0; t <= static_cast<int>(kSlots) && s < kSlots; ++t) {
+  for (int t = 0; t <= S && s < S; ++t) {
     const uint32_t bit = 1u << s;
     const uint32_t old = atomicAnd(v.masks + b, ~bit);
     if (old & bit) {
-      st_relaxed64(v.buckets + static_cast<uint64_t>(b) * kSlots + s, word);
+      st_relaxed64(v.buckets + static_cast<uint64_t>(b) * S + s, word);
       return true;
     }
-    s = old ? static_cast<uint32_t>(__ffs(old) - 1) : kSlots;
+    s = old ? static_cast<uint32_t>(__ffs(old) - 1) : S;
   }
   return false;
 }
@@ -153,14 +154,18 @@ __device__ __forceinline__ bool claim_store(const View& v, uint32_t b, uint32_t 
 // reads EMPTY as its victim and stops); the CAS then fails and this claim
 // looks for another bit.  Bits only get cleared in this phase, so the loop
 // ends after at most S successful fetch_ands.
-__device__ __forceinline__ bool claim_cas(const View& v, uint32_t b, uint64_t word) {
-  uint32_t fm = ld_relaxed32(v.masks + b);
-  for (int t = 0; t <= 2 * static_cast<int>(kSlots) && fm; ++t) {
+template <int S>
+__device__ __forceinline__ bool claim_cas(const View& v, uint32_t b, uint64_t word,
+                                          uint32_t hint = 0) {
+  // `hint`: a free mask of bucket b read moments ago, used as the first guess
+  // (the fetch_and result is the authority either way)
+  uint32_t fm = hint ? hint : ld_relaxed32(v.masks + b);
+  for (int t = 0; t <= 2 * S && fm; ++t) {
     const uint32_t s = __ffs(fm) - 1;
     const uint32_t bit = 1u << s;
     const uint32_t old = atomicAnd(v.masks + b, ~bit);
     if (old & bit) {
-      unsigned long long* sp = ull(v.buckets + static_cast<uint64_t>(b) * kSlots + s);
+      unsigned long long* sp = ull(v.buckets + static_cast<uint64_t>(b) * S + s);
       if (atomicCAS(sp, kEmptyWord, word) == kEmptyWord) return true;
       fm = ld_relaxed32(v.masks + b);
     } else {
@@ -170,18 +175,17 @@ __device__ __forceinline__ bool claim_cas(const View& v, uint32_t b, uint64_t wo
   return false;
 }
 
+// The bucket lock serialises evictors of one bucket (Algorithm 3).  Every
+// access it protects is an L2 atomic whose result has returned before the
+// unlock issues, so neither side needs a fence.
 __device__ __forceinline__ bool lock_bucket(const View& v, uint32_t b) {
   for (uint32_t t = 0; t < v.lock_spin_limit; ++t) {
-    if (atomicCAS(v.locks + b, 0u, 1u) == 0u) {
-      __threadfence();
-      return true;
-    }
+    if (atomicCAS(v.locks + b, 0u, 1u) == 0u) return true;
     __nanosleep(64);
   }
   return false;
 }
 __device__ __forceinline__ void unlock_bucket(const View& v, uint32_t b) {
-  __threadfence();
   atomicExch(v.locks + b, 0u);
 }
 
@@ -211,38 +215,52 @@ struct LaneCounters {
   bool reserved = false, contract = false;
 };
 
+// Lane geometry of a bucket of S slots read as 16-byte fragments: L lanes per
+// bucket, Q buckets per load instruction.
+template <int S>
+struct Geo {
+  static constexpr int L = S / 2;
+  static constexpr int Q = 32 / L;
+  static constexpr unsigned LM = (L >= 32) ? 0xFFFFFFFFu : ((1u << L) - 1u);
+};
+
 // One probe round over the 32 ops of a warp.  `need` has bit j set when op j
-// (held by lane j, its home lane) must read bucket `myb` this round.  The ops
-// go in four groups of eight; in a group, load u (u = 0..3) of the 16-lane
-// half h reads the bucket of op 2u + h, 16 bytes (two slots) per lane, so the
-// four loads of a lane cover eight buckets.  Match-and-elect (Section III-F)
-// is a ballot per load: the lowest matching lane of a half is the winner, and
-// one shuffle per load hands the matched value to every home lane, which then
-// reads its own op's outcome out of the warp-uniform ballots.  A home lane
-// that must update the matched slot (erase, replace) does the single CAS
-// itself: the expected word is (value << 32 | key), both of which it now holds.
-template <int MODE>
+// (held by lane j, its home lane) must read bucket `myb` this round.  Load u
+// (u = 0..3) of lane group q (L lanes) reads the bucket of op Q*u + q of the
+// current group of 4Q ops, 16 bytes (two slots) per lane, so each load
+// instruction probes Q buckets.  Match-and-elect (Section III-F) is a ballot
+// per load: the lowest matching lane of a group is the winner, and one shuffle
+// per load hands the matched value to every home lane, which then reads its
+// own op's outcome out of the warp-uniform ballots.  A home lane that must
+// update the matched slot (erase, replace) does the single CAS itself: the
+// expected word is (value << 32 | key), both of which it now holds.
+template <int MODE, int S>
 __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb, uint32_t key,
                                       uint32_t val, uint32_t op, int lane, bool& done,
                                       uint8_t& st, uint32_t& outv, uint32_t& fcnt,
                                       uint32_t& fslot, LaneCounters& cnt) {
   constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
-  const int h = lane >> 4;
-  const int hl = lane & 15;
-  const int my_g = lane >> 3, my_j = lane & 7, my_u = my_j >> 1, my_h = my_j & 1;
+  constexpr int L = Geo<S>::L, Q = Geo<S>::Q;
+  constexpr unsigned LM = Geo<S>::LM;
+  constexpr int G = 4 * Q;   // ops per group
+  constexpr int NG = 32 / G; // groups per warp
+  constexpr unsigned GM = (G >= 32) ? 0xFFFFFFFFu : ((1u << G) - 1u);
+  const int q = lane / L;
+  const int ql = lane % L;
+  const int my_g = lane / G, my_j = lane % G, my_u = my_j / Q, my_q = my_j % Q;
 #pragma unroll 1
-  for (int g = 0; g < 4; ++g) {
-    const unsigned gneed = (need >> (8 * g)) & 0xFFu;
+  for (int g = 0; g < NG; ++g) {
+    const unsigned gneed = (need >> (G * g)) & GM;
     if (!gneed) continue;
     uint64_t wa[4], wb[4];
     uint32_t kq[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int src = 8 * g + 2 * u + h;
+      const int src = G * g + Q * u + q;
       const uint32_t bq = __shfl_sync(kFull, myb, src);
       kq[u] = __shfl_sync(kFull, key, src);
-      if ((gneed >> (2 * u + h)) & 1u) {
-        const uint64_t* p = v.buckets + static_cast<uint64_t>(bq) * kSlots + 2 * hl;
+      if ((gneed >> (Q * u + q)) & 1u) {
+        const uint64_t* p = v.buckets + static_cast<uint64_t>(bq) * S + 2 * ql;
         if (MODE == kModeFind)
           ld_frag_ro(p, wa[u], wb[u]);
         else
@@ -263,8 +281,8 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
       const unsigned el = kIns ? __ballot_sync(kFull, wa[u] == kEmptyWord) : 0u;
       const unsigned eh = kIns ? __ballot_sync(kFull, wb[u] == kEmptyWord) : 0u;
       const uint32_t cv = lo ? val_of(wa[u]) : val_of(wb[u]);
-      const unsigned hm = (m >> (16 * my_h)) & 0xFFFFu;
-      const uint32_t x = __shfl_sync(kFull, cv, 16 * my_h + (hm ? __ffs(hm) - 1 : 0));
+      const unsigned hm = (m >> (L * my_q)) & LM;
+      const uint32_t x = __shfl_sync(kFull, cv, L * my_q + (hm ? __ffs(hm) - 1 : 0));
       if (u == my_u) {
         my_m = m;
         my_mh = mh;
@@ -274,7 +292,7 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
       }
     }
     if (my_g == g && ((gneed >> my_j) & 1u)) {
-      const unsigned hm = (my_m >> (16 * my_h)) & 0xFFFFu;
+      const unsigned hm = (my_m >> (L * my_q)) & LM;
       if (hm) {
         done = true;
         const uint32_t opk = MODE == kModeMixed
@@ -286,8 +304,8 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
           st = ST_FOUND;
         } else {
           const uint32_t w = __ffs(hm) - 1;
-          const uint32_t slot = 2 * w + ((my_mh >> (16 * my_h + w)) & 1u);
-          uint64_t* sp = v.buckets + static_cast<uint64_t>(myb) * kSlots + slot;
+          const uint32_t slot = 2 * w + ((my_mh >> (L * my_q + w)) & 1u);
+          uint64_t* sp = v.buckets + static_cast<uint64_t>(myb) * S + slot;
           const uint64_t cur = pack(key, got);
           if (opk == OP_ERASE) {
             // Algorithm 4: CAS the slot to EMPTY, then publish the free bit.
@@ -310,45 +328,53 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
           }
         }
       } else if (kIns) {
-        const unsigned ev = (my_el >> (16 * my_h)) & 0xFFFFu;
-        const unsigned od = (my_eh >> (16 * my_h)) & 0xFFFFu;
+        const unsigned ev = (my_el >> (L * my_q)) & LM;
+        const unsigned od = (my_eh >> (L * my_q)) & LM;
         fcnt = __popc(ev) + __popc(od);
-        const uint32_t se = ev ? 2u * (__ffs(ev) - 1) : kSlots;
-        const uint32_t so = od ? 2u * (__ffs(od) - 1) + 1u : kSlots;
+        const uint32_t se = ev ? 2u * (__ffs(ev) - 1) : S;
+        const uint32_t so = od ? 2u * (__ffs(od) - 1) + 1u : S;
         fslot = se < so ? se : so;
       }
     }
   }
 }
 
-// Insert batches probe both candidate buckets of an op in one round: in load
-// u of group g, half-warp 0 reads the BitHash1 bucket and half-warp 1 the
-// BitHash2 bucket of op 4g + u.  An insert of a new key needs both buckets
-// anyway (step 1 must rule the key out of both before step 2 claims), so this
-// halves the dependent probe rounds of the find-shaped probe() above.  On a
-// match the home lane replaces the value with one CAS (Algorithm 1);
+// Insert batches probe both candidate buckets of an op in one round: the two
+// lane groups of a pair read the BitHash1 and the BitHash2 bucket of one op,
+// P = Q / 2 ops per load instruction.  An insert of a new key needs both
+// buckets anyway (step 1 must rule the key out of both before step 2 claims),
+// so this halves the dependent probe rounds of the find-shaped probe() above.
+// On a match the home lane replaces the value with one CAS (Algorithm 1);
 // otherwise it records each bucket's free count and first free slot.
+template <int S>
 __device__ __forceinline__ void probe_pair(const View& v, unsigned need, uint32_t b1,
                                            uint32_t b2, uint32_t key, uint32_t val, int lane,
                                            bool& done, uint8_t& st, uint32_t& f1, uint32_t& s1,
                                            uint32_t& f2, uint32_t& s2, LaneCounters& cnt) {
-  const int h = lane >> 4;
-  const int hl = lane & 15;
-  const int my_g = lane >> 2, my_u = lane & 3;
+  constexpr int L = Geo<S>::L, Q = Geo<S>::Q;
+  constexpr unsigned LM = Geo<S>::LM;
+  constexpr int P = Q / 2;    // ops per load instruction
+  constexpr int G = 4 * P;    // ops per group
+  constexpr int NG = 32 / G;  // groups per warp
+  constexpr unsigned GM = (1u << G) - 1u;
+  constexpr unsigned PM = (2 * L >= 32) ? 0xFFFFFFFFu : ((1u << (2 * L)) - 1u);
+  const int q = lane / L;
+  const int ql = lane % L;
+  const int my_g = lane / G, my_j = lane % G, my_u = my_j / P, my_p = my_j % P;
 #pragma unroll 1
-  for (int g = 0; g < 8; ++g) {
-    const unsigned gneed = (need >> (4 * g)) & 0xFu;
+  for (int g = 0; g < NG; ++g) {
+    const unsigned gneed = (need >> (G * g)) & GM;
     if (!gneed) continue;
     uint64_t wa[4], wb[4];
     uint32_t kq[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int src = 4 * g + u;
+      const int src = G * g + P * u + (q >> 1);
       const uint32_t q1 = __shfl_sync(kFull, b1, src);
       const uint32_t q2 = __shfl_sync(kFull, b2, src);
       kq[u] = __shfl_sync(kFull, key, src);
-      if ((gneed >> u) & 1u) {
-        const uint64_t* p = v.buckets + static_cast<uint64_t>(h ? q2 : q1) * kSlots + 2 * hl;
+      if ((gneed >> (P * u + (q >> 1))) & 1u) {
+        const uint64_t* p = v.buckets + static_cast<uint64_t>((q & 1) ? q2 : q1) * S + 2 * ql;
         ld_frag(p, wa[u], wb[u]);
       } else {
         wa[u] = kEmptyWord;
@@ -366,7 +392,8 @@ __device__ __forceinline__ void probe_pair(const View& v, unsigned need, uint32_
       const unsigned el = __ballot_sync(kFull, wa[u] == kEmptyWord);
       const unsigned eh = __ballot_sync(kFull, wb[u] == kEmptyWord);
       const uint32_t cv = lo ? val_of(wa[u]) : val_of(wb[u]);
-      const uint32_t x = __shfl_sync(kFull, cv, m ? __ffs(m) - 1 : 0);
+      const unsigned pm = (m >> (2 * L * my_p)) & PM;
+      const uint32_t x = __shfl_sync(kFull, cv, 2 * L * my_p + (pm ? __ffs(pm) - 1 : 0));
       if (u == my_u) {
         my_m = m;
         my_mh = mh;
@@ -375,29 +402,31 @@ __device__ __forceinline__ void probe_pair(const View& v, unsigned need, uint32_
         got = x;
       }
     }
-    if (my_g == g && ((gneed >> my_u) & 1u)) {
-      if (my_m) {
-        // the lowest matching lane: the BitHash1 half wins when both match
+    if (my_g == g && ((gneed >> my_j) & 1u)) {
+      const int base = 2 * L * my_p;
+      const unsigned pm = (my_m >> base) & PM;
+      if (pm) {
+        // the lowest matching lane: the BitHash1 group wins when both match
         done = true;
         st = ST_REPLACED;
-        const uint32_t w = __ffs(my_m) - 1;
-        const uint32_t slot = 2 * (w & 15) + ((my_mh >> w) & 1u);
-        const uint32_t b = w < 16 ? b1 : b2;
-        uint64_t* sp = v.buckets + static_cast<uint64_t>(b) * kSlots + slot;
+        const uint32_t w = __ffs(pm) - 1;
+        const uint32_t slot = 2 * (w % L) + ((my_mh >> (base + w)) & 1u);
+        const uint32_t b = w < static_cast<uint32_t>(L) ? b1 : b2;
+        uint64_t* sp = v.buckets + static_cast<uint64_t>(b) * S + slot;
         const uint64_t cur = pack(key, got);
         if (atomicCAS(ull(sp), cur, pack(key, val)) == cur)
           cnt.replaced += 1;
         else
           cnt.contract = true;
       } else {
-        const unsigned e0 = my_el & 0xFFFFu, o0 = my_eh & 0xFFFFu;
-        const unsigned e1 = my_el >> 16, o1 = my_eh >> 16;
+        const unsigned e0 = (my_el >> base) & LM, o0 = (my_eh >> base) & LM;
+        const unsigned e1 = (my_el >> (base + L)) & LM, o1 = (my_eh >> (base + L)) & LM;
         f1 = __popc(e0) + __popc(o0);
         f2 = __popc(e1) + __popc(o1);
-        const uint32_t a0 = e0 ? 2u * (__ffs(e0) - 1) : kSlots;
-        const uint32_t a1 = o0 ? 2u * (__ffs(o0) - 1) + 1u : kSlots;
-        const uint32_t c0 = e1 ? 2u * (__ffs(e1) - 1) : kSlots;
-        const uint32_t c1 = o1 ? 2u * (__ffs(o1) - 1) + 1u : kSlots;
+        const uint32_t a0 = e0 ? 2u * (__ffs(e0) - 1) : S;
+        const uint32_t a1 = o0 ? 2u * (__ffs(o0) - 1) + 1u : S;
+        const uint32_t c0 = e1 ? 2u * (__ffs(e1) - 1) : S;
+        const uint32_t c1 = o1 ? 2u * (__ffs(o1) - 1) + 1u : S;
         s1 = a0 < a1 ? a0 : a1;
         s2 = c0 < c1 ? c0 : c1;
       }
@@ -441,7 +470,7 @@ __device__ __forceinline__ void flush_counters(const View& v, LaneCounters& cnt,
 
 // Ops [32c, 32c + 32) of a batch of n ops on the table of `v`.  Full-bucket
 // inserts go to the overflow list, tagged with `seg` when the list keeps tags.
-template <int MODE>
+template <int MODE, int S>
 __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const OpPtrs a,
                                           uint32_t c, uint64_t n, const List ovf, uint32_t seg,
                                           LaneCounters& cnt, int lane) {
@@ -468,20 +497,20 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
   bool done = !live;
   uint8_t st = reserved ? ST_RESERVED : ST_NOT_FOUND;
   uint32_t outv = 0;
-  uint32_t f1 = 0, s1 = kSlots, f2 = 0, s2 = kSlots;
+  uint32_t f1 = 0, s1 = S, f2 = 0, s2 = S;
 
   // Probe the BitHash1 bucket of every op, then the BitHash2 bucket of the
   // ops still unresolved (Section IV-B: WCME over the d = 2 candidates).
   unsigned need = __ballot_sync(kFull, !done);
   if (MODE == kModeInsert) {
     cnt.probes += 2 * __popc(need);
-    if (need) probe_pair(v, need, b1, b2, key, val, lane, done, st, f1, s1, f2, s2, cnt);
+    if (need) probe_pair<S>(v, need, b1, b2, key, val, lane, done, st, f1, s1, f2, s2, cnt);
   } else {
     cnt.probes += __popc(need);
-    if (need) probe<MODE>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt);
+    if (need) probe<MODE, S>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt);
     need = __ballot_sync(kFull, !done);
     cnt.probes += __popc(need);
-    if (need) probe<MODE>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt);
+    if (need) probe<MODE, S>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt);
   }
 
   // The stash (Section IV-A step 4) holds keys that found no bucket room.
@@ -521,8 +550,8 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
     const uint32_t ob = first1 ? b2 : b1, os = first1 ? s2 : s1;
     bool placed = false;
     if (f1 + f2 > 0) {
-      placed = claim_store(v, tb, ts, word);
-      if (!placed && ob != tb) placed = claim_store(v, ob, os, word);
+      placed = claim_store<S>(v, tb, ts, word);
+      if (!placed && ob != tb) placed = claim_store<S>(v, ob, os, word);
     }
     if (placed) {
       done = true;
@@ -563,7 +592,7 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
   }
 }
 
-template <int MODE>
+template <int MODE, int S>
 __global__ void __launch_bounds__(kOpsThreads, HIVE_OPS_MIN_BLOCKS)
     k_ops(View v, OpPtrs a, uint64_t n, List ovf) {
   const int lane = threadIdx.x & 31;
@@ -574,7 +603,7 @@ __global__ void __launch_bounds__(kOpsThreads, HIVE_OPS_MIN_BLOCKS)
   const uint32_t stash_n = v.ctrl->stash_n;
   LaneCounters cnt;
   for (uint32_t c = warp0; c < nchunks; c += nwarps)
-    run_chunk<MODE>(v, stash_n, a, c, n, ovf, 0, cnt, lane);
+    run_chunk<MODE, S>(v, stash_n, a, c, n, ovf, 0, cnt, lane);
   flush_counters(v, cnt, lane);
 }
 
@@ -599,9 +628,13 @@ __device__ __forceinline__ bool stash_reserve(const View& v) {
   return false;
 }
 
-// Counters of the eviction kernel, kept by lane 0 of a warp.
+// Counters of the eviction kernel, kept by lane 0 of a warp, and the stash
+// word the warp holds in reserve.  A warp works one item at a time, so one
+// reservation covers all its chains: it is kept across items that end in a
+// bucket and renewed only after a chain used it for a stash append.
 struct OvfCounters {
   unsigned claim = 0, rounds = 0, locks = 0, to = 0, stash = 0, pend = 0, added = 0;
+  Ctrl* reserved_in = nullptr;  // control block of the table the reservation belongs to
 };
 
 __device__ __forceinline__ void flush_ovf_counters(const View& v, OvfCounters& oc, int lane) {
@@ -618,13 +651,22 @@ __device__ __forceinline__ void flush_ovf_counters(const View& v, OvfCounters& o
     if (oc.stash) atomicAdd(&c->stats[kStStashed], static_cast<unsigned long long>(oc.stash));
     if (oc.pend) atomicAdd(&c->stats[kStPending], static_cast<unsigned long long>(oc.pend));
   }
+  Ctrl* keep = oc.reserved_in;  // a reservation outlives the counters
   oc = OvfCounters();
+  oc.reserved_in = keep;
+}
+
+// Gives back a warp's unused stash reservation.
+__device__ __forceinline__ void release_reservation(OvfCounters& oc, int lane) {
+  if (lane == 0 && oc.reserved_in) atomicSub(&oc.reserved_in->stash_claims, 1u);
+  oc.reserved_in = nullptr;
 }
 
 // Steps 3-4 for one insert whose candidate buckets were full (warp-wide).
 // `idx` is the caller's op index (kNoOp for a word moved by a merge); the
 // outcome goes to status[idx].  With `resizable`, an insert that finds no room
 // at all joins the pending list, else it is reported FULL.
+template <int S>
 __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uint32_t idx,
                                               uint32_t seg, uint8_t* status, int resizable,
                                               const List& pend, OvfCounters& oc, int lane) {
@@ -635,11 +677,18 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
   // 0: needs eviction, 1: placed, 2: stashed, 3: no room (pending)
   int outcome = 0;
   if (lane == 0) {
-    if (claim_cas(v, b1, word0) || (b2 != b1 && claim_cas(v, b2, word0))) {
+    // both free masks in one round trip; claim where a bit is free
+    const uint32_t m1 = ld_relaxed32(v.masks + b1);
+    const uint32_t m2 = ld_relaxed32(v.masks + b2);
+    if ((m1 && claim_cas<S>(v, b1, word0)) || (b2 != b1 && m2 && claim_cas<S>(v, b2, word0))) {
       outcome = 1;
       ++oc.claim;
-    } else if (!stash_reserve(v)) {
-      outcome = 3;
+    } else {
+      if (oc.reserved_in != v.ctrl) {
+        if (oc.reserved_in) atomicSub(&oc.reserved_in->stash_claims, 1u);
+        oc.reserved_in = stash_reserve(v) ? v.ctrl : nullptr;
+      }
+      if (!oc.reserved_in) outcome = 3;
     }
   }
   outcome = __shfl_sync(kFull, outcome, 0);
@@ -651,31 +700,36 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
     for (uint32_t r = 0; r < v.max_evictions; ++r) {
       // Look ahead: each lane checks whether the word in its slot could move
       // to its other candidate bucket without a further eviction.
-      const uint64_t w = ld_relaxed64(v.buckets + static_cast<uint64_t>(b) * kSlots + lane);
-      bool good = false;
+      const uint64_t w =
+          lane < S ? ld_relaxed64(v.buckets + static_cast<uint64_t>(b) * S + lane) : kEmptyWord;
+      uint32_t am = 0;  // free mask of this word's other candidate bucket
       if (w != kEmptyWord) {
         const uint32_t k = key_of(w);
         const uint32_t a1 = lh_bucket(bithash1(k), v.M, v.p);
         const uint32_t a2 = lh_bucket(bithash2(k), v.M, v.p);
         const uint32_t alt = (a1 == b) ? a2 : a1;
-        if (alt != b) good = ld_relaxed32(v.masks + alt) != 0u;
+        if (alt != b) am = ld_relaxed32(v.masks + alt);
       }
-      const unsigned gm = __ballot_sync(kFull, good);
+      const unsigned gm = __ballot_sync(kFull, am != 0u);
+      const bool has_empty = __ballot_sync(kFull, lane < S && w == kEmptyWord) != 0u;
       int res = 0;  // 0: evicted `victim`, 1: placed, 2: lock wait gave up
       uint64_t victim = kEmptyWord;
+      const uint32_t vs = gm ? static_cast<uint32_t>(__ffs(gm) - 1)
+                             : ((bithash2(key_of(cur)) + r) & (S - 1));
+      const uint32_t vmask = __shfl_sync(kFull, am, vs);
       if (lane == 0) {
         ++oc.rounds;
-        const uint32_t vs = gm ? static_cast<uint32_t>(__ffs(gm) - 1)
-                               : ((bithash2(key_of(cur)) + r) & (kSlots - 1));
         if (!lock_bucket(v, b)) {
           res = 2;
           ++oc.to;
         } else {
           ++oc.locks;
-          if (claim_cas(v, b, cur)) {
+          // a free slot shows as an EMPTY word (a claimed, unpublished one
+          // too: the exchange below then reads EMPTY and stops)
+          if (has_empty && claim_cas<S>(v, b, cur)) {
             res = 1;
           } else {
-            victim = atomicExch(ull(v.buckets + static_cast<uint64_t>(b) * kSlots + vs), cur);
+            victim = atomicExch(ull(v.buckets + static_cast<uint64_t>(b) * S + vs), cur);
             res = (victim == kEmptyWord) ? 1 : 0;
           }
           unlock_bucket(v, b);
@@ -697,16 +751,21 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
       if (nb == b) break;  // both candidates are this bucket: no alternative
       b = nb;
       int ok = 0;
-      if (lane == 0) ok = claim_cas(v, b, cur);
+      if (lane == 0) ok = claim_cas<S>(v, b, cur, vmask);
       if (__shfl_sync(kFull, ok, 0)) {
         placed = true;
         break;
       }
     }
     if (lane == 0) {
-      if (placed) {
+      if (placed && oc.reserved_in && ld_relaxed32(&v.ctrl->stash_claims) >= v.stash_cap) {
+        // every free stash word is reserved: give this one back so that a
+        // waiting warp can go on
         atomicSub(&v.ctrl->stash_claims, 1u);
-      } else {
+        oc.reserved_in = nullptr;
+      }
+      if (!placed) {
+        oc.reserved_in = nullptr;  // this append uses the reservation
         const unsigned pos = atomicAdd(&v.ctrl->stash_tail, 1u);
         st_relaxed64(v.stash_kv + pos, cur);
         ++oc.stash;
@@ -734,6 +793,7 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
   }
 }
 
+template <int S>
 __global__ void __launch_bounds__(kOvfThreads)
     k_overflow(View v, List in, List pend, int resizable, uint8_t* __restrict__ status) {
   const int lane = threadIdx.x & 31;
@@ -742,7 +802,8 @@ __global__ void __launch_bounds__(kOvfThreads)
   const unsigned total = *in.count;
   OvfCounters oc;
   for (unsigned it = warp0; it < total; it += nwarps)
-    overflow_item(v, in.words[it], in.idx[it], 0, status, resizable, pend, oc, lane);
+    overflow_item<S>(v, in.words[it], in.idx[it], 0, status, resizable, pend, oc, lane);
+  release_reservation(oc, lane);
   flush_ovf_counters(v, oc, lane);
 }
 
@@ -774,6 +835,7 @@ __device__ void block_bitonic(uint64_t* a, unsigned P) {
 
 // One CTA maintains the stash of the table of `v`; `smem` holds
 // kMaintSmemWords words.
+template <int S>
 __device__ void maint_body(const View& v, uint64_t* smem) {
   __shared__ unsigned s_reins, s_live;
   Ctrl* c = v.ctrl;
@@ -797,10 +859,10 @@ __device__ void maint_body(const View& v, uint64_t* smem) {
     const uint32_t b1 = lh_bucket(bithash1(k), v.M, v.p);
     const uint32_t b2 = lh_bucket(bithash2(k), v.M, v.p);
     const uint32_t m1 = ld_relaxed32(v.masks + b1);
-    bool ok = m1 && claim_store(v, b1, __ffs(m1) - 1, w);
+    bool ok = m1 && claim_store<S>(v, b1, __ffs(m1) - 1, w);
     if (!ok) {
       const uint32_t m2 = ld_relaxed32(v.masks + b2);
-      ok = m2 && claim_store(v, b2, __ffs(m2) - 1, w);
+      ok = m2 && claim_store<S>(v, b2, __ffs(m2) - 1, w);
     }
     if (ok) {
       v.stash_kv[j] = kEmptyWord;
@@ -844,9 +906,10 @@ __device__ void maint_body(const View& v, uint64_t* smem) {
   }
 }
 
+template <int S>
 __global__ void __launch_bounds__(kMaintThreads) k_maint(View v) {
   extern __shared__ uint64_t smem[];
-  maint_body(v, smem);
+  maint_body<S>(v, smem);
 }
 
 // ----------------------------------------------------------------------------
@@ -858,11 +921,12 @@ __global__ void __launch_bounds__(kMaintThreads) k_maint(View v) {
 // when neither candidate address equals the source under the new state; it
 // then belongs to the partner, where the movers are packed from slot 0 by a
 // ballot-rank compaction.
+template <int S>
 __device__ __forceinline__ void split_pair(const View& v, uint32_t src, uint32_t half, int lane) {
   const uint32_t dst = src + half;
-  uint64_t* sb = v.buckets + static_cast<uint64_t>(src) * kSlots;
-  uint64_t* db = v.buckets + static_cast<uint64_t>(dst) * kSlots;
-  const uint64_t word = sb[lane];
+  uint64_t* sb = v.buckets + static_cast<uint64_t>(src) * S;
+  uint64_t* db = v.buckets + static_cast<uint64_t>(dst) * S;
+  const uint64_t word = lane < S ? sb[lane] : kEmptyWord;
   bool mv = false;
   if (word != kEmptyWord) {
     const uint32_t k = key_of(word);
@@ -876,27 +940,31 @@ __device__ __forceinline__ void split_pair(const View& v, uint32_t src, uint32_t
     sb[lane] = kEmptyWord;
   }
   if (lane == 0) {
+    constexpr uint32_t kValid = S >= 32 ? 0xFFFFFFFFu : ((1u << S) - 1u);
     v.masks[src] |= mm;
     const int nm = __popc(mm);
-    v.masks[dst] = nm >= 32 ? 0u : (0xFFFFFFFFu << nm);
+    v.masks[dst] = nm >= 32 ? 0u : ((0xFFFFFFFFu << nm) & kValid);
   }
 }
 
+template <int S>
 __global__ void __launch_bounds__(256) k_split(View v, uint32_t src0, uint32_t count, uint32_t half) {
   const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= count) return;
-  split_pair(v, src0 + w, half, threadIdx.x & 31);
+  split_pair<S>(v, src0 + w, half, threadIdx.x & 31);
 }
 
 // Contraction pre-check: how many words of the batch's high buckets do not
 // fit into the free slots of their low partner.
+template <int S>
 __global__ void __launch_bounds__(256) k_merge_excess(View v, uint32_t count) {
   const int lane = threadIdx.x & 31;
   const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= count) return;
   const uint32_t low = v.p + w;
   const uint32_t high = low + v.M + 1u;
-  const uint64_t word = v.buckets[static_cast<uint64_t>(high) * kSlots + lane];
+  const uint64_t word =
+      lane < S ? v.buckets[static_cast<uint64_t>(high) * S + lane] : kEmptyWord;
   const int live = __popc(__ballot_sync(kFull, word != kEmptyWord));
   const int fr = __popc(v.masks[low]);
   if (lane == 0 && live > fr) atomicAdd(&v.ctrl->merge_excess, static_cast<unsigned>(live - fr));
@@ -906,15 +974,16 @@ __global__ void __launch_bounds__(256) k_merge_excess(View v, uint32_t count) {
 // `v` carrying the state after this launch.  Live words take the free slots
 // of the low bucket in rank order (select the r-th free bit); words that do
 // not fit go to the overflow list and are placed by the eviction kernel.
+template <int S>
 __global__ void __launch_bounds__(256) k_merge(View v, uint32_t count, List ovf) {
   const int lane = threadIdx.x & 31;
   const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= count) return;
   const uint32_t low = v.p + w;
   const uint32_t high = low + v.M + 1u;
-  uint64_t* lb = v.buckets + static_cast<uint64_t>(low) * kSlots;
-  uint64_t* hb = v.buckets + static_cast<uint64_t>(high) * kSlots;
-  const uint64_t word = hb[lane];
+  uint64_t* lb = v.buckets + static_cast<uint64_t>(low) * S;
+  uint64_t* hb = v.buckets + static_cast<uint64_t>(high) * S;
+  const uint64_t word = lane < S ? hb[lane] : kEmptyWord;
   const bool live = word != kEmptyWord;
   const unsigned lm = __ballot_sync(kFull, live);
   const unsigned rank = __popc(lm & ((1u << lane) - 1u));
@@ -939,13 +1008,13 @@ __global__ void __launch_bounds__(256) k_merge(View v, uint32_t count, List ovf)
       ovf.idx[r] = kNoOp;
     }
   }
-  hb[lane] = kEmptyWord;
+  if (lane < S) hb[lane] = kEmptyWord;
   if (lane == 0) {
     const unsigned used = __popc(lm) < nfree ? __popc(lm) : nfree;
     uint32_t m = fr;
     for (unsigned t = 0; t < used; ++t) m &= m - 1u;
     v.masks[low] = m;
-    v.masks[high] = 0xFFFFFFFFu;
+    v.masks[high] = S >= 32 ? 0xFFFFFFFFu : ((1u << S) - 1u);
   }
 }
 
@@ -971,6 +1040,7 @@ __device__ __forceinline__ OpPtrs seg_ptrs(const MultiSeg& S) {
 
 // Each warp takes a contiguous run of chunks, so it changes table only at
 // segment boundaries and flushes its counters there.
+template <int S>
 __global__ void __launch_bounds__(kOpsThreads, HIVE_MULTI_MIN_BLOCKS)
     k_multi_ops(const MultiHdr* __restrict__ hdr, const MultiSeg* __restrict__ segs,
                 const View* __restrict__ views, List ovf) {
@@ -1002,13 +1072,14 @@ __global__ void __launch_bounds__(kOpsThreads, HIVE_MULTI_MIN_BLOCKS)
       stash_n = v.ctrl->stash_n;
       a = seg_ptrs(segs[s]);
     }
-    run_chunk<kModeMixed>(v, stash_n, a, c - segs[s].chunk0, segs[s].n, ovf, s, cnt, lane);
+    run_chunk<kModeMixed, S>(v, stash_n, a, c - segs[s].chunk0, segs[s].n, ovf, s, cnt, lane);
   }
   flush_counters(v, cnt, lane);
 }
 
 // Steps 3-4 for the overflow list of a multi-table batch.  Inserts that find
 // no room are reported FULL (a resizable table grows before its next batch).
+template <int S>
 __global__ void __launch_bounds__(kOvfThreads)
     k_multi_overflow(const MultiSeg* __restrict__ segs, const View* __restrict__ views, List in) {
   const int lane = threadIdx.x & 31;
@@ -1016,29 +1087,32 @@ __global__ void __launch_bounds__(kOvfThreads)
   const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
   const unsigned total = *in.count;
   const List none{nullptr, nullptr, nullptr, nullptr};
+  OvfCounters oc;
   for (unsigned it = warp0; it < total; it += nwarps) {
     const uint32_t sg = in.seg[it];
     const View v = views[segs[sg].table];
-    OvfCounters oc;
-    overflow_item(v, in.words[it], in.idx[it], sg, segs[sg].status, 0, none, oc, lane);
+    overflow_item<S>(v, in.words[it], in.idx[it], sg, segs[sg].status, 0, none, oc, lane);
     flush_ovf_counters(v, oc, lane);
   }
+  release_reservation(oc, lane);
 }
 
 // One CTA per table of the batch: stash maintenance (exits at once when
 // nothing changed).  The grid covers every table of the group, so a captured
 // graph serves batches of any composition.
+template <int S>
 __global__ void __launch_bounds__(256)
     k_multi_maint(const MultiHdr* __restrict__ hdr, const View* __restrict__ views,
                   const uint32_t* __restrict__ touched) {
   extern __shared__ uint64_t smem[];
   if (blockIdx.x >= hdr->n_touched) return;
-  maint_body(views[touched[blockIdx.x]], smem);
+  maint_body<S>(views[touched[blockIdx.x]], smem);
 }
 
 // One wave of split launches over many tables: warp w runs pair
 // w - pair0 of the job whose range holds w.  Jobs of one wave touch disjoint
 // buckets (a table appears in a wave with splits of one round only).
+template <int S>
 __global__ void __launch_bounds__(256)
     k_multi_split(const MultiJob* __restrict__ jobs, uint32_t n_jobs, uint32_t total_pairs,
                   const View* __restrict__ views) {
@@ -1053,7 +1127,7 @@ __global__ void __launch_bounds__(256)
   View v = views[J.table];
   v.M = J.M;
   v.p = J.p;
-  split_pair(v, J.src0 + (w - J.pair0), J.half, threadIdx.x & 31);
+  split_pair<S>(v, J.src0 + (w - J.pair0), J.half, threadIdx.x & 31);
 }
 
 // Size and stash fill of each table of the batch, for the host's resize
@@ -1069,7 +1143,13 @@ __global__ void k_multi_gather(const MultiHdr* __restrict__ hdr, const View* __r
   out[2 * t + 1] = (static_cast<unsigned long long>(c->err) << 32) | c->stash_claims;
 }
 
-template <int MODE>
+__global__ void k_fill_u32(uint32_t* __restrict__ p, uint64_t n, uint32_t value) {
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+    p[i] = value;
+}
+
+template <int MODE, int S>
 cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys,
                          const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
                          uint8_t* status, List ovf, const Launch& L, cudaStream_t s) {
@@ -1080,8 +1160,24 @@ cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   const OpPtrs a{ops, keys, vals, vals_out, found, status};
-  k_ops<MODE><<<static_cast<unsigned>(blocks), kOpsThreads, 0, s>>>(v, a, n, ovf);
+  k_ops<MODE, S><<<static_cast<unsigned>(blocks), kOpsThreads, 0, s>>>(v, a, n, ovf);
   return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_ops_s(int mode, const View& v, const uint8_t* ops, const uint32_t* keys,
+                         const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
+                         uint8_t* status, List ovf, const Launch& L, cudaStream_t s) {
+  switch (mode) {
+    case kModeFind:
+      return launch_ops_t<kModeFind, S>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
+    case kModeInsert:
+      return launch_ops_t<kModeInsert, S>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
+    case kModeErase:
+      return launch_ops_t<kModeErase, S>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
+    default:
+      return launch_ops_t<kModeMixed, S>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
+  }
 }
 
 }  // namespace
@@ -1089,27 +1185,27 @@ cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys
 cudaError_t launch_ops(int mode, const View& v, const uint8_t* ops, const uint32_t* keys,
                        const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
                        uint8_t* status, List ovf, const Launch& L, cudaStream_t s) {
-  switch (mode) {
-    case kModeFind:
-      return launch_ops_t<kModeFind>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
-    case kModeInsert:
-      return launch_ops_t<kModeInsert>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
-    case kModeErase:
-      return launch_ops_t<kModeErase>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
-    default:
-      return launch_ops_t<kModeMixed>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
-  }
+  if (v.S == 16)
+    return launch_ops_s<16>(mode, v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
+  return launch_ops_s<32>(mode, v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
 }
 
 cudaError_t launch_overflow(const View& v, List in, List pend, int resizable, uint8_t* status,
                             const Launch& L, cudaStream_t s) {
   const unsigned blocks = static_cast<unsigned>(L.num_sms * L.ovf_blocks_per_sm);
-  k_overflow<<<blocks, kOvfThreads, 0, s>>>(v, in, pend, resizable, status);
+  if (v.S == 16)
+    k_overflow<16><<<blocks, kOvfThreads, 0, s>>>(v, in, pend, resizable, status);
+  else
+    k_overflow<32><<<blocks, kOvfThreads, 0, s>>>(v, in, pend, resizable, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_maintenance(const View& v, cudaStream_t s) {
-  k_maint<<<1, kMaintThreads, kMaintSmemWords * sizeof(uint64_t), s>>>(v);
+  constexpr size_t smem = kMaintSmemWords * sizeof(uint64_t);
+  if (v.S == 16)
+    k_maint<16><<<1, kMaintThreads, smem, s>>>(v);
+  else
+    k_maint<32><<<1, kMaintThreads, smem, s>>>(v);
   return cudaGetLastError();
 }
 
@@ -1117,21 +1213,30 @@ cudaError_t launch_split(const View& v_new, uint32_t src0, uint32_t count, uint3
                          cudaStream_t s) {
   if (!count) return cudaSuccess;
   const unsigned blocks = (count * 32u + 255u) / 256u;
-  k_split<<<blocks, 256, 0, s>>>(v_new, src0, count, half);
+  if (v_new.S == 16)
+    k_split<16><<<blocks, 256, 0, s>>>(v_new, src0, count, half);
+  else
+    k_split<32><<<blocks, 256, 0, s>>>(v_new, src0, count, half);
   return cudaGetLastError();
 }
 
 cudaError_t launch_merge_excess(const View& v_new, uint32_t count, cudaStream_t s) {
   if (!count) return cudaSuccess;
   const unsigned blocks = (count * 32u + 255u) / 256u;
-  k_merge_excess<<<blocks, 256, 0, s>>>(v_new, count);
+  if (v_new.S == 16)
+    k_merge_excess<16><<<blocks, 256, 0, s>>>(v_new, count);
+  else
+    k_merge_excess<32><<<blocks, 256, 0, s>>>(v_new, count);
   return cudaGetLastError();
 }
 
 cudaError_t launch_merge(const View& v_new, uint32_t count, List ovf, cudaStream_t s) {
   if (!count) return cudaSuccess;
   const unsigned blocks = (count * 32u + 255u) / 256u;
-  k_merge<<<blocks, 256, 0, s>>>(v_new, count, ovf);
+  if (v_new.S == 16)
+    k_merge<16><<<blocks, 256, 0, s>>>(v_new, count, ovf);
+  else
+    k_merge<32><<<blocks, 256, 0, s>>>(v_new, count, ovf);
   return cudaGetLastError();
 }
 
@@ -1143,32 +1248,53 @@ cudaError_t launch_count_inserts(const uint8_t* ops, uint64_t n, unsigned* out, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_multi_ops(const MultiHdr* hdr, const MultiSeg* segs, const View* views, List ovf,
-                             const Launch& L, cudaStream_t s) {
-  k_multi_ops<<<static_cast<unsigned>(L.num_sms * L.multi_blocks_per_sm), kOpsThreads, 0, s>>>(
-      hdr, segs, views, ovf);
+cudaError_t launch_fill_u32(uint32_t* p, uint64_t n, uint32_t value, cudaStream_t s) {
+  if (!n) return cudaSuccess;
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  k_fill_u32<<<static_cast<unsigned>(blocks), 256, 0, s>>>(p, n, value);
   return cudaGetLastError();
 }
 
-cudaError_t launch_multi_overflow(const MultiSeg* segs, const View* views, List in,
+cudaError_t launch_multi_ops(int S, const MultiHdr* hdr, const MultiSeg* segs, const View* views,
+                             List ovf, const Launch& L, cudaStream_t s) {
+  const unsigned blocks = static_cast<unsigned>(L.num_sms * L.multi_blocks_per_sm);
+  if (S == 16)
+    k_multi_ops<16><<<blocks, kOpsThreads, 0, s>>>(hdr, segs, views, ovf);
+  else
+    k_multi_ops<32><<<blocks, kOpsThreads, 0, s>>>(hdr, segs, views, ovf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_overflow(int S, const MultiSeg* segs, const View* views, List in,
                                   const Launch& L, cudaStream_t s) {
-  k_multi_overflow<<<static_cast<unsigned>(L.num_sms * L.ovf_blocks_per_sm), kOvfThreads, 0, s>>>(
-      segs, views, in);
+  const unsigned blocks = static_cast<unsigned>(L.num_sms * L.ovf_blocks_per_sm);
+  if (S == 16)
+    k_multi_overflow<16><<<blocks, kOvfThreads, 0, s>>>(segs, views, in);
+  else
+    k_multi_overflow<32><<<blocks, kOvfThreads, 0, s>>>(segs, views, in);
   return cudaGetLastError();
 }
 
-cudaError_t launch_multi_maint(const MultiHdr* hdr, const View* views, const uint32_t* touched,
-                               uint32_t max_tables, cudaStream_t s) {
+cudaError_t launch_multi_maint(int S, const MultiHdr* hdr, const View* views,
+                               const uint32_t* touched, uint32_t max_tables, cudaStream_t s) {
   if (!max_tables) return cudaSuccess;
-  k_multi_maint<<<max_tables, 256, kMaintSmemWords * sizeof(uint64_t), s>>>(hdr, views, touched);
+  constexpr size_t smem = kMaintSmemWords * sizeof(uint64_t);
+  if (S == 16)
+    k_multi_maint<16><<<max_tables, 256, smem, s>>>(hdr, views, touched);
+  else
+    k_multi_maint<32><<<max_tables, 256, smem, s>>>(hdr, views, touched);
   return cudaGetLastError();
 }
 
-cudaError_t launch_multi_split(const MultiJob* jobs, uint32_t n_jobs, uint32_t total_pairs,
+cudaError_t launch_multi_split(int S, const MultiJob* jobs, uint32_t n_jobs, uint32_t total_pairs,
                                const View* views, cudaStream_t s) {
   if (!total_pairs) return cudaSuccess;
   const unsigned blocks = static_cast<unsigned>((static_cast<uint64_t>(total_pairs) * 32 + 255) / 256);
-  k_multi_split<<<blocks, 256, 0, s>>>(jobs, n_jobs, total_pairs, views);
+  if (S == 16)
+    k_multi_split<16><<<blocks, 256, 0, s>>>(jobs, n_jobs, total_pairs, views);
+  else
+    k_multi_split<32><<<blocks, 256, 0, s>>>(jobs, n_jobs, total_pairs, views);
   return cudaGetLastError();
 }
 
@@ -1179,27 +1305,34 @@ cudaError_t launch_multi_gather(const MultiHdr* hdr, const View* views, const ui
   return cudaGetLastError();
 }
 
-cudaError_t query_occupancy(Launch* L) {
+namespace {
+template <int S>
+cudaError_t occupancy_s(Launch* L) {
+  int b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeInsert, S>,
+                                                                kOpsThreads, 0);
+  if (e != cudaSuccess) return e;
+  L->ops_blocks_per_sm = b > 0 ? b : 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_multi_ops<S>, kOpsThreads, 0);
+  if (e != cudaSuccess) return e;
+  L->multi_blocks_per_sm = b > 0 ? b : 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_overflow<S>, kOvfThreads, 0);
+  if (e != cudaSuccess) return e;
+  L->ovf_blocks_per_sm = b > 0 ? b : 1;
+  const int smem = static_cast<int>(kMaintSmemWords * sizeof(uint64_t));
+  e = cudaFuncSetAttribute(k_multi_maint<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_maint<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+}  // namespace
+
+cudaError_t query_occupancy(Launch* L, int S) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&L->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  int b = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeInsert>, kOpsThreads, 0);
-  if (e != cudaSuccess) return e;
-  L->ops_blocks_per_sm = b > 0 ? b : 1;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_multi_ops, kOpsThreads, 0);
-  if (e != cudaSuccess) return e;
-  L->multi_blocks_per_sm = b > 0 ? b : 1;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_overflow, kOvfThreads, 0);
-  if (e != cudaSuccess) return e;
-  L->ovf_blocks_per_sm = b > 0 ? (b < 2 ? b : 2) : 1;
-  e = cudaFuncSetAttribute(k_multi_maint, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(kMaintSmemWords * sizeof(uint64_t)));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_maint, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(kMaintSmemWords * sizeof(uint64_t)));
+  return S == 16 ? occupancy_s<16>(L) : occupancy_s<32>(L);
 }
 
 }  // namespace hive

@@ -116,9 +116,10 @@ hive_status enqueue_fixed(hive_multi* m, cudaStream_t s) {
   const View* dv = views_of(m, m->d_stage);
   const uint32_t* tc = touched_of(m, m->d_stage);
   MCK(cudaMemsetAsync(m->d_count, 0, sizeof(unsigned), s));
-  MCK(launch_multi_ops(hd, segs_of(m, m->d_stage), dv, ovf, m->L, s));
-  MCK(launch_multi_overflow(segs_of(m, m->d_stage), dv, ovf, m->L, s));
-  MCK(launch_multi_maint(hd, dv, tc, nt, s));
+  const int S = static_cast<int>(m->tables[0]->S);
+  MCK(launch_multi_ops(S, hd, segs_of(m, m->d_stage), dv, ovf, m->L, s));
+  MCK(launch_multi_overflow(S, segs_of(m, m->d_stage), dv, ovf, m->L, s));
+  MCK(launch_multi_maint(S, hd, dv, tc, nt, s));
   MCK(launch_multi_gather(hd, dv, tc, nt, m->d_gather, s));
   MCK(cudaMemcpyAsync(m->h_gather, m->d_gather, 2 * sizeof(unsigned long long) * nt,
                       cudaMemcpyDeviceToHost, s));
@@ -183,6 +184,10 @@ hive_status hive_multi_create(hive_table* const* tables, uint32_t n_tables, uint
     if (!tables[i]) {
       delete m;
       return mfail(HIVE_ERR_INVALID_ARG, "a table handle is NULL");
+    }
+    if (tables[i]->S != tables[0]->S) {
+      delete m;
+      return mfail(HIVE_ERR_INVALID_ARG, "all tables of a group need the same bucket_slots");
     }
     m->tables.push_back(tables[i]);
     m->any_resizable |= tables[i]->cfg.resizable != 0;
@@ -335,8 +340,8 @@ hive_status hive_multi_execute(hive_multi* m, const hive_segment* segs, uint32_t
     const uint32_t e = w + 1 < m->wave_begin.size() ? m->wave_begin[w + 1]
                                                     : static_cast<uint32_t>(m->jobs.size());
     const MultiJob& last = m->jobs[e - 1];
-    MCK(launch_multi_split(jobs_of(m, m->d_stage) + b, e - b, last.pair0 + last.count,
-                           views_of(m, m->d_stage), s));
+    MCK(launch_multi_split(static_cast<int>(m->tables[0]->S), jobs_of(m, m->d_stage) + b, e - b,
+                           last.pair0 + last.count, views_of(m, m->d_stage), s));
   }
 
   // (3) the fixed part

@@ -165,11 +165,12 @@ class HiveTable:
                  resizable: bool = False, max_evictions: int = 16, resize_batch: int = 1024,
                  stash_permille: int = 10, grow=(9, 10), shrink=(2, 5),
                  placement: int = PLACE_BALANCED, lock_spin_limit: int | None = None,
-                 blocks_per_sm: int = 0, stream=None):
+                 blocks_per_sm: int = 0, bucket_slots: int = 32, stream=None):
         self._L = load_library()
         cfg = Config()
         self._L.hive_config_default(C.byref(cfg))
         cfg.initial_slots = int(initial_slots)
+        cfg.bucket_slots = int(bucket_slots)
         cfg.max_slots = int(max_slots if max_slots is not None else initial_slots)
         cfg.max_evictions = int(max_evictions)
         cfg.resize_batch = int(resize_batch)

@@ -52,7 +52,7 @@ def test_host_validation_without_gpu(lib):
     assert b"NULL" in lib.hive_last_error()
     bad = hive.Config()
     lib.hive_config_default(C.byref(bad))
-    bad.bucket_slots = 16
+    bad.bucket_slots = 24
     h = C.c_void_p()
     assert lib.hive_create(C.byref(bad), None, C.byref(h)) == 1
     bad.bucket_slots = 32

@@ -73,18 +73,19 @@ def _run(H, tables, dicts, policies, batches, use_graph, rng, seed0, skip_prob=0
         for t, tb in enumerate(tables):
             if policies[t] is not None:
                 policies[t].shrink(len(dicts[t]))
-                assert tb.capacity() == S * policies[t].state[0], (b, t, tb.capacity(), policies[t].state)
-            code, where = oracle.check_image(tb.dump(), S, dicts[t], policies[t])
+                assert tb.capacity() == policies[t].s.S * policies[t].state[0], (b, t, tb.capacity(), policies[t].state)
+            img = tb.dump()
+            code, where = oracle.check_image(img, img["S"], dicts[t], policies[t])
             assert code == 0, (b, t, code, where)
             assert tb.check() == 0
     m.close()
 
 
-@pytest.mark.parametrize("use_graph", [False, True])
-def test_multi_fixed_tables(H, use_graph):
+@pytest.mark.parametrize("use_graph,bs", [(False, 32), (True, 32), (True, 16)])
+def test_multi_fixed_tables(H, use_graph, bs):
     rng = np.random.default_rng(3 if use_graph else 4)
     sizes = [1 << int(x) for x in rng.integers(10, 17, 24)]
-    tables = [H.HiveTable(sz) for sz in sizes]
+    tables = [H.HiveTable(sz, bucket_slots=bs) for sz in sizes]
     dicts = [oracle.Dict() for _ in tables]
     for i, (tb, d) in enumerate(zip(tables, dicts)):  # preload to about half
         k, _ = W.take_keys(500 + i, 0, sizes[i] // 2)

@@ -46,17 +46,18 @@ def check_status(got, exp, what):
 
 def check_image(t, d, policy=None):
     img = t.dump()
-    code, where = oracle.check_image(img, S, d, policy)
+    code, where = oracle.check_image(img, img["S"], d, policy)
     assert code == 0, f"invariant {code} fails at {where}"
     assert img["size"] == len(d)
     return img
 
 
-def test_plain_2e20_phases(H):
+@pytest.mark.parametrize("bs", [32, 16])
+def test_plain_2e20_phases(H, bs):
     """Fixed 2^20-slot table: insert 838,861 (80%), find all plus as many
-    absent keys, erase a seeded half, find again."""
+    absent keys, erase a seeded half, find again (32- and 16-slot buckets)."""
     w = W.plain_phases(seed=1)
-    t = H.HiveTable(1 << 20)
+    t = H.HiveTable(1 << 20, bucket_slots=bs)
     d = oracle.Dict()
     check_status(t.insert(up(H, w["insert_keys"]), up(H, w["insert_vals"])),
                  d.insert(w["insert_keys"], w["insert_vals"]), "insert")
@@ -118,14 +119,15 @@ def test_replace_then_find(H):
     t.close()
 
 
-@pytest.mark.parametrize("load_pct,slots", [(95, 1 << 12), (99, 1 << 12), (95, 1 << 16),
-                                            (98, 1 << 16)])
-def test_high_load_eviction_and_stash(H, load_pct, slots):
+@pytest.mark.parametrize("load_pct,slots,bs", [(95, 1 << 12, 32), (99, 1 << 12, 32),
+                                               (95, 1 << 16, 32), (98, 1 << 16, 32),
+                                               (95, 1 << 12, 16), (98, 1 << 16, 16)])
+def test_high_load_eviction_and_stash(H, load_pct, slots, bs):
     """Near-full tables exercise steps 3 and 4 (eviction, stash)."""
     n = slots * load_pct // 100
     keys, c = W.take_keys(17 + load_pct, 0, n)
     vals = W.values_for(keys, 17)
-    t = H.HiveTable(slots, stash_permille=50)
+    t = H.HiveTable(slots, stash_permille=50, bucket_slots=bs)
     d = oracle.Dict()
     # two halves so the second insert meets a loaded table
     for part in (keys[: n // 2], keys[n // 2:]):
@@ -168,10 +170,10 @@ def test_full_table_reports_full(H):
     t.close()
 
 
-@pytest.mark.parametrize("seed", [1, 2, 3])
-def test_mixed_batches(H, seed):
+@pytest.mark.parametrize("seed,bs", [(1, 32), (2, 32), (3, 32), (4, 16)])
+def test_mixed_batches(H, seed, bs):
     rng = np.random.default_rng(seed)
-    t = H.HiveTable(1 << 16)
+    t = H.HiveTable(1 << 16, bucket_slots=bs)
     d = oracle.Dict()
     live, c = W.take_keys(seed, 0, 30_000)
     check_status(t.insert(up(H, live), up(H, W.values_for(live, seed))),
@@ -190,12 +192,14 @@ def test_mixed_batches(H, seed):
     t.close()
 
 
-def test_resizable_grow_and_shrink(H):
+@pytest.mark.parametrize("bs", [32, 16])
+def test_resizable_grow_and_shrink(H, bs):
     """Linear-hashing growth and contraction track the oracle's capacity model
     call by call, with invariants (including the load-factor band) after each."""
     K = 64
-    t = H.HiveTable(1 << 12, max_slots=1 << 22, resizable=True, resize_batch=K, shrink=(2, 5))
-    pol = oracle.Policy((1 << 12) // S, (1 << 22) // S, K=K, shrink=(2, 5))
+    t = H.HiveTable(1 << 12, max_slots=1 << 22, resizable=True, resize_batch=K, shrink=(2, 5),
+                    bucket_slots=bs)
+    pol = oracle.Policy((1 << 12) // bs, (1 << 22) // bs, S=bs, K=K, shrink=(2, 5))
     d = oracle.Dict()
     rng = np.random.default_rng(9)
     live = np.zeros(0, np.uint32)
@@ -212,7 +216,7 @@ def test_resizable_grow_and_shrink(H):
         pol.shrink(len(d))
         check_status(st, est, f"batch {b}")
         assert np.array_equal(H.to_host_u32(vo), ev)
-        assert t.capacity() == S * pol.state[0], (b, t.capacity(), pol.state)
+        assert t.capacity() == bs * pol.state[0], (b, t.capacity(), pol.state)
         live, _ = d.dump()
         check_image(t, d, pol)
     assert t.stats()["splits"] > 0 and t.stats()["merges"] > 0
