@@ -204,6 +204,14 @@ hive_status hive_size(hive_table* t, uint64_t* out, void* stream);
  * no synchronisation. */
 hive_status hive_reserve(hive_table* t, uint64_t slots, void* stream);
 
+/* Device memory of the table in bytes: `committed` is backed by physical
+ * memory now, `reserved` is the most it can grow to.  A resizable table keeps
+ * its buckets on CUDA virtual memory: it reserves the address range of
+ * max_slots at creation, maps physical memory as splits add buckets and
+ * returns it after merges, so committed memory follows the capacity (the
+ * other arrays are allocated at their maximum).  Host-side, no sync. */
+hive_status hive_memory(hive_table* t, uint64_t* committed, uint64_t* reserved);
+
 /* Current slot capacity S * nBuckets (host-side state, no synchronisation). */
 hive_status hive_capacity(hive_table* t, uint64_t* slots_out);
 

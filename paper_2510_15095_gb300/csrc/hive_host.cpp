@@ -161,6 +161,8 @@ hive_status split_step(hive_table* t, cudaStream_t s, bool* did) {
   SplitPlan pl{};
   *did = plan_split(t, &pl);
   if (!*did) return HIVE_OK;
+  hive_status st = ensure_committed(t, s);
+  if (st != HIVE_OK) return st;
   View v = make_view(t);
   v.M = pl.M;
   v.p = pl.p;
@@ -185,6 +187,8 @@ hive_status grow_for(hive_table* t, uint64_t n_ins, cudaStream_t s) {
       continue;
     }
     if (have) {
+      hive_status st = ensure_committed(t, s);
+      if (st != HIVE_OK) return st;
       View v = make_view(t);
       v.M = acc.M;
       v.p = acc.p;
@@ -194,6 +198,8 @@ hive_status grow_for(hive_table* t, uint64_t n_ins, cudaStream_t s) {
     have = true;
   }
   if (have) {
+    hive_status st = ensure_committed(t, s);
+    if (st != HIVE_OK) return st;
     View v = make_view(t);
     v.M = acc.M;
     v.p = acc.p;
@@ -256,6 +262,12 @@ bool hive::under_shrink(const hive_table* t, uint64_t live, uint64_t nb) {
 // next maintenance pass look at it.
 hive_status hive::mark_stash_dirty(hive_table* t, cudaStream_t s) {
   HIVE_CK(cudaMemsetAsync(&t->ctrl->stash_dirty, 1, 1, s));
+  return HIVE_OK;
+}
+
+hive_status hive::ensure_committed(hive_table* t, cudaStream_t s) {
+  if (!t->vmm) return HIVE_OK;
+  HIVE_CK(grow_commit(&t->bucket_vm, t->nb * t->S * sizeof(uint64_t), s));
   return HIVE_OK;
 }
 
@@ -322,6 +334,12 @@ hive_status hive::contract_table(hive_table* t, cudaStream_t s) {
     st = readback(t, s);
     if (st != HIVE_OK) return st;
     t->size_host = t->host_ctrl->size;
+    if (t->vmm) {
+      // the work above has completed; buckets past nb are empty and unused,
+      // so their memory goes back (one chunk is kept to damp oscillation)
+      const size_t need = t->nb * t->S * sizeof(uint64_t) + t->bucket_vm.gran;
+      if (t->bucket_vm.committed > need + 3 * t->bucket_vm.gran) grow_decommit(&t->bucket_vm, need);
+    }
   }
   return HIVE_OK;
 }
@@ -433,9 +451,23 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
 
   cudaError_t e = cudaGetDevice(&t->device);
   if (e == cudaSuccess) e = query_occupancy(&t->L, static_cast<int>(S));
-  if (e == cudaSuccess && cfg->blocks_per_sm && static_cast<int>(cfg->blocks_per_sm) < t->L.ops_blocks_per_sm)
-    t->L.ops_blocks_per_sm = static_cast<int>(cfg->blocks_per_sm);
-  if (e == cudaSuccess) e = cudaMalloc(&t->buckets, t->nb_max * S * sizeof(uint64_t));
+  if (e == cudaSuccess && cfg->blocks_per_sm) {
+    const int cap = static_cast<int>(cfg->blocks_per_sm);
+    t->L.ops_blocks_per_sm = std::min(t->L.ops_blocks_per_sm, cap);
+    t->L.staged_blocks_per_sm = std::min(t->L.staged_blocks_per_sm, cap);
+  }
+  if (e == cudaSuccess && cfg->resizable) {
+    // reserve the address range of nb_max buckets, back only nb_init of them
+    if (grow_reserve(&t->bucket_vm, t->nb_max * S * sizeof(uint64_t), t->device) == cudaSuccess) {
+      t->vmm = true;
+      t->buckets = reinterpret_cast<uint64_t*>(t->bucket_vm.base);
+      e = grow_commit(&t->bucket_vm, t->nb_init * S * sizeof(uint64_t), s);
+    } else {
+      cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess && !t->vmm)
+    e = cudaMalloc(&t->buckets, t->nb_max * S * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->masks, t->nb_max * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->locks, t->nb_max * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->stash_kv, t->stash_alloc * sizeof(uint64_t));
@@ -444,7 +476,7 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
   if (e == cudaSuccess) e = cudaMallocHost(&t->host_ctrl, sizeof(Ctrl));
   if (e == cudaSuccess) {
     std::memset(t->host_ctrl, 0, sizeof(Ctrl));
-    e = cudaMemsetAsync(t->buckets, 0xFF, t->nb_max * S * sizeof(uint64_t), s);
+    if (!t->vmm) e = cudaMemsetAsync(t->buckets, 0xFF, t->nb_max * S * sizeof(uint64_t), s);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(t->masks, 0xFF, t->nb_max * sizeof(uint32_t), s);
   if (e == cudaSuccess && S < 32) e = launch_fill_u32(t->masks, t->nb_max, (1u << S) - 1u, s);
@@ -463,7 +495,10 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
 hive_status hive_destroy(hive_table* t) {
   if (!t) return HIVE_OK;
   cudaDeviceSynchronize();
-  cudaFree(t->buckets);
+  if (t->vmm)
+    grow_free(&t->bucket_vm);
+  else
+    cudaFree(t->buckets);
   cudaFree(t->masks);
   cudaFree(t->locks);
   cudaFree(t->stash_kv);
@@ -592,6 +627,20 @@ hive_status hive_reserve(hive_table* t, uint64_t slots, void* stream) {
     if ((st = mark_stash_dirty(t, s)) != HIVE_OK) return st;
     HIVE_LAUNCH(t, HIVE_K_MAINT, s, launch_maintenance(make_view(t), s));
   }
+  return HIVE_OK;
+}
+
+hive_status hive_memory(hive_table* t, uint64_t* committed, uint64_t* reserved) {
+  hive_status st = check_table(t);
+  if (st != HIVE_OK) return st;
+  if (!committed || !reserved) return fail(HIVE_ERR_INVALID_ARG, "outputs must not be NULL");
+  const uint64_t bucket_max = t->nb_max * t->S * sizeof(uint64_t);
+  const uint64_t bucket_now = t->vmm ? t->bucket_vm.committed : bucket_max;
+  const uint64_t other = t->nb_max * 2 * sizeof(uint32_t) + t->stash_alloc * sizeof(uint64_t) +
+                         t->stash_cap * sizeof(uint32_t) + sizeof(Ctrl) +
+                         t->list_cap * (t->cfg.resizable ? 24 : 12);
+  *committed = bucket_now + other;
+  *reserved = bucket_max + other;
   return HIVE_OK;
 }
 

@@ -118,7 +118,8 @@ enum OpMode : int { kModeFind = 0, kModeInsert = 1, kModeErase = 2, kModeMixed =
 
 struct Launch {
   int num_sms;
-  int ops_blocks_per_sm;
+  int ops_blocks_per_sm;     // bulk kernel, fragments loaded from global memory
+  int staged_blocks_per_sm;  // bulk kernel, probes staged in shared memory
   int ovf_blocks_per_sm;
   int multi_blocks_per_sm;
 };
@@ -149,6 +150,21 @@ cudaError_t launch_multi_gather(const MultiHdr* hdr, const View* views, const ui
                                 uint32_t max_tables, unsigned long long* out, cudaStream_t s);
 cudaError_t query_occupancy(Launch* L, int S);
 
+}  // namespace hive
+
+namespace hive {
+// A device array on CUDA virtual memory: `reserved` bytes of address space,
+// the first `committed` of them backed by physical chunks of `gran` bytes.
+struct GrowArray {
+  uint64_t base = 0;
+  size_t reserved = 0, committed = 0, gran = 0;
+  int device = 0;
+  std::vector<uint64_t> handles;  // one physical allocation per chunk
+};
+cudaError_t grow_reserve(GrowArray* a, size_t max_bytes, int device);
+cudaError_t grow_commit(GrowArray* a, size_t bytes, cudaStream_t s);  // new chunks filled 0xFF
+void grow_decommit(GrowArray* a, size_t bytes);  // caller ensures no kernel uses the tail
+void grow_free(GrowArray* a);
 }  // namespace hive
 
 // Device staging of the host-buffer calls (hive_*_host), two slots.
@@ -199,6 +215,8 @@ struct hive_table {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> ev_pool;
   HostIO io;  // host-buffer call staging (allocated on first use)
+  hive::GrowArray bucket_vm;  // resizable tables: buckets on virtual memory
+  bool vmm = false;
 };
 
 // Helpers shared by the translation units of the library (hive_host.cpp
@@ -219,6 +237,8 @@ bool under_shrink(const hive_table* t, uint64_t live, uint64_t nb);
 hive_status contract_table(hive_table* t, cudaStream_t s);
 hive_status mark_stash_dirty(hive_table* t, cudaStream_t s);
 void free_staging(hive_table* t);  // releases the host-buffer call staging
+// Resizable tables on virtual memory: back buckets [0, nb) with physical memory.
+hive_status ensure_committed(hive_table* t, cudaStream_t s);
 bool table_view(const hive_table* t, View* v, Launch* L, bool* resizable);
 void set_last_error(const std::string& msg);  // text returned by hive_last_error()
 }  // namespace hive

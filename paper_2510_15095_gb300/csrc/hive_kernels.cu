@@ -33,6 +33,17 @@ constexpr int kOpsThreads = 256;
 #ifndef HIVE_MULTI_MIN_BLOCKS
 #define HIVE_MULTI_MIN_BLOCKS 3  // the multi-table bulk kernel also holds a table view per warp
 #endif
+#ifndef HIVE_STAGED_MODES
+// Bulk-kernel modes (bit kModeFind, kModeInsert, ...) whose probes are staged
+// in shared memory by bulk copies; the others load fragments straight from
+// global memory.  Staging pays for insert batches, whose paired probe reads
+// both buckets of every op; finds and mixed batches run faster with four
+// direct-load blocks per SM than with three staged ones.
+#define HIVE_STAGED_MODES 0x2
+#endif
+#ifndef HIVE_STAGED_MIN_BLOCKS
+#define HIVE_STAGED_MIN_BLOCKS 3  // 64 KB of staging per block: three blocks fit an SM
+#endif
 #ifndef HIVE_OPS_MIN_BLOCKS
 #define HIVE_OPS_MIN_BLOCKS 4  // resident 256-thread blocks per SM the bulk kernel is built for
 #endif
@@ -123,6 +134,48 @@ __device__ __forceinline__ void st_relaxed64(uint64_t* p, uint64_t v) {
 
 __device__ __forceinline__ unsigned long long* ull(uint64_t* p) {
   return reinterpret_cast<unsigned long long*>(p);
+}
+
+// ---- TMA bulk copies (cp.async.bulk) into shared memory, mbarrier-tracked ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// One bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) writes to the same memory.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void lds_frag(const uint64_t* p, uint64_t& a, uint64_t& b) {
+  asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(smem_u32(p)));
 }
 
 // ----------------------------------------------------------------------------
@@ -224,21 +277,108 @@ struct Geo {
   static constexpr unsigned LM = (L >= 32) ? 0xFFFFFFFFu : ((1u << L) - 1u);
 };
 
+// ---- Shared-memory staging of bucket reads (TMA bulk copies) ----
+//
+// A kernel that stages its probes gives each warp one mbarrier and a buffer of
+// kStageWords words (8 KB): every bucket a probe round needs -- the 32 ops'
+// buckets of a single-bucket round, or both candidate buckets of 32 (S = 16)
+// or 16 (S = 32) ops of a paired round -- is requested with one whole-bucket
+// cp.async.bulk per bucket, so the warp has all of them in flight at once
+// without holding registers, and the barrier counts the arriving bytes.  The
+// evaluation then reads 16-byte fragments out of shared memory in the same
+// order the global-memory probe reads them.  A wait that does not end within
+// kMbarSpinLimit tries raises the table's sticky TIMEOUT error, marks the
+// stage dead and redoes the round from global memory.
+constexpr int kStageWords = 1024;
+constexpr int kStageBytesPerWarp = 8 * (kStageWords + 2);
+constexpr uint32_t kMbarSpinLimit = 1u << 22;
+constexpr size_t kStageSmemBytes = static_cast<size_t>(kOpsThreads / 32) * kStageBytesPerWarp;
+
+struct Stage {
+  uint64_t* bar;   // mbarrier
+  uint64_t* buf;   // kStageWords words, 16-byte aligned
+  uint32_t phase;  // parity of the barrier's current phase
+  bool dead;       // a wait gave up: copies may still land, the buffer is not reused
+};
+
+// Sets up the calling warp's stage in the kernel's dynamic shared memory.
+__device__ __forceinline__ Stage stage_init(uint64_t* smem, int warp_in_block, int lane) {
+  Stage sg;
+  uint64_t* base = smem + static_cast<size_t>(warp_in_block) * (kStageBytesPerWarp / 8);
+  sg.bar = base;
+  sg.buf = base + 2;
+  sg.phase = 0;
+  sg.dead = false;
+  if (lane == 0) mbar_init(sg.bar, 1);
+  __syncwarp();
+  return sg;
+}
+
+// Before a warp exits: a stage whose wait gave up may still receive bytes;
+// wait (bounded) for them so that no copy lands after the block has left.
+__device__ __forceinline__ void stage_drain(Stage& sg) {
+  if (!sg.dead) return;
+  bool ok = false;
+  for (uint32_t it = 0; it < kMbarSpinLimit && !ok; ++it) ok = mbar_try_wait(sg.bar, sg.phase ^ 1u);
+}
+
+// Issues the copies of one staged round and waits for them (warp-wide).
+// PAIR = false: op j (bit j of `need`, j < 32) copies bucket x1 of lane j to
+// buffer bucket j.  PAIR = true: ops [o0, o0 + 512 / S) copy buckets x1 and x2
+// of their lanes to buffer buckets 2 (j - o0) and 2 (j - o0) + 1.  Returns
+// false, with the stage marked dead and the error raised, if the wait gave up.
+template <int S, bool PAIR>
+__device__ __forceinline__ bool stage_round(const View& v, Stage& sg, unsigned need, int o0,
+                                            uint32_t x1, uint32_t x2, int lane) {
+  constexpr uint32_t kBucketBytes = S * 8u;
+  fence_proxy_async();  // earlier fragment reads of the buffer come before the new copies
+  __syncwarp();
+  if (lane == 0) mbar_arrive_expect_tx(sg.bar, __popc(need) * (PAIR ? 2u : 1u) * kBucketBytes);
+  __syncwarp();
+  if (!PAIR) {
+    if ((need >> lane) & 1u)
+      bulk_g2s(sg.buf + lane * S, v.buckets + static_cast<uint64_t>(x1) * S, kBucketBytes, sg.bar);
+  } else {
+    constexpr int BO = kStageWords / (2 * S);
+#pragma unroll
+    for (int k = 0; k < (2 * BO) / 32; ++k) {
+      const int bi = lane + 32 * k;
+      const int op = o0 + (bi >> 1);
+      const uint32_t y1 = __shfl_sync(kFull, x1, op & 31);
+      const uint32_t y2 = __shfl_sync(kFull, x2, op & 31);
+      if ((need >> op) & 1u)
+        bulk_g2s(sg.buf + bi * S, v.buckets + static_cast<uint64_t>((bi & 1) ? y2 : y1) * S,
+                 kBucketBytes, sg.bar);
+    }
+  }
+  bool ok = false;
+  for (uint32_t it = 0; it < kMbarSpinLimit && !ok; ++it) ok = mbar_try_wait(sg.bar, sg.phase);
+  sg.phase ^= 1u;
+  if (__any_sync(kFull, !ok)) {  // never expected
+    sg.dead = true;
+    if (lane == 0) atomicOr(&v.ctrl->err, kErrTimeout);
+    return false;
+  }
+  return true;
+}
+
 // One probe round over the 32 ops of a warp.  `need` has bit j set when op j
 // (held by lane j, its home lane) must read bucket `myb` this round.  Load u
 // (u = 0..3) of lane group q (L lanes) reads the bucket of op Q*u + q of the
 // current group of 4Q ops, 16 bytes (two slots) per lane, so each load
-// instruction probes Q buckets.  Match-and-elect (Section III-F) is a ballot
-// per load: the lowest matching lane of a group is the winner, and one shuffle
-// per load hands the matched value to every home lane, which then reads its
-// own op's outcome out of the warp-uniform ballots.  A home lane that must
-// update the matched slot (erase, replace) does the single CAS itself: the
-// expected word is (value << 32 | key), both of which it now holds.
-template <int MODE, int S>
+// instruction probes Q buckets -- from global memory, or with STAGED from the
+// warp's shared-memory copy `sbuf` of the round's buckets (buffer bucket j =
+// op j).  Match-and-elect (Section III-F) is a ballot per load: the lowest
+// matching lane of a group is the winner, and one shuffle per load hands the
+// matched value to every home lane, which then reads its own op's outcome out
+// of the warp-uniform ballots.  A home lane that must update the matched slot
+// (erase, replace) does the single CAS itself: the expected word is
+// (value << 32 | key), both of which it now holds.
+template <int MODE, int S, bool STAGED>
 __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb, uint32_t key,
                                       uint32_t val, uint32_t op, int lane, bool& done,
                                       uint8_t& st, uint32_t& outv, uint32_t& fcnt,
-                                      uint32_t& fslot, LaneCounters& cnt) {
+                                      uint32_t& fslot, LaneCounters& cnt, const uint64_t* sbuf) {
   constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
   constexpr int L = Geo<S>::L, Q = Geo<S>::Q;
   constexpr unsigned LM = Geo<S>::LM;
@@ -257,17 +397,27 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int src = G * g + Q * u + q;
-      const uint32_t bq = __shfl_sync(kFull, myb, src);
-      kq[u] = __shfl_sync(kFull, key, src);
-      if ((gneed >> (Q * u + q)) & 1u) {
-        const uint64_t* p = v.buckets + static_cast<uint64_t>(bq) * S + 2 * ql;
-        if (MODE == kModeFind)
-          ld_frag_ro(p, wa[u], wb[u]);
-        else
-          ld_frag(p, wa[u], wb[u]);
+      if (STAGED) {
+        kq[u] = __shfl_sync(kFull, key, src);
+        if ((gneed >> (Q * u + q)) & 1u) {
+          lds_frag(sbuf + src * S + 2 * ql, wa[u], wb[u]);
+        } else {
+          wa[u] = kEmptyWord;
+          wb[u] = kEmptyWord;
+        }
       } else {
-        wa[u] = kEmptyWord;
-        wb[u] = kEmptyWord;
+        const uint32_t bq = __shfl_sync(kFull, myb, src);
+        kq[u] = __shfl_sync(kFull, key, src);
+        if ((gneed >> (Q * u + q)) & 1u) {
+          const uint64_t* p = v.buckets + static_cast<uint64_t>(bq) * S + 2 * ql;
+          if (MODE == kModeFind)
+            ld_frag_ro(p, wa[u], wb[u]);
+          else
+            ld_frag(p, wa[u], wb[u]);
+        } else {
+          wa[u] = kEmptyWord;
+          wb[u] = kEmptyWord;
+        }
       }
     }
     unsigned my_m = 0, my_mh = 0, my_el = 0, my_eh = 0;
@@ -344,25 +494,28 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
 // P = Q / 2 ops per load instruction.  An insert of a new key needs both
 // buckets anyway (step 1 must rule the key out of both before step 2 claims),
 // so this halves the dependent probe rounds of the find-shaped probe() above.
-// On a match the home lane replaces the value with one CAS (Algorithm 1);
-// otherwise it records each bucket's free count and first free slot.
-template <int S>
+// Covers the op groups of ops [o0, o1); with STAGED the fragments come from
+// `sbuf`, which holds op j's buckets at buffer buckets 2 (j - o0) and
+// 2 (j - o0) + 1.  On a match the home lane replaces the value with one CAS
+// (Algorithm 1); otherwise it records each bucket's free count and first
+// free slot.
+template <int S, bool STAGED>
 __device__ __forceinline__ void probe_pair(const View& v, unsigned need, uint32_t b1,
                                            uint32_t b2, uint32_t key, uint32_t val, int lane,
                                            bool& done, uint8_t& st, uint32_t& f1, uint32_t& s1,
-                                           uint32_t& f2, uint32_t& s2, LaneCounters& cnt) {
+                                           uint32_t& f2, uint32_t& s2, LaneCounters& cnt,
+                                           const uint64_t* sbuf, int o0, int o1) {
   constexpr int L = Geo<S>::L, Q = Geo<S>::Q;
   constexpr unsigned LM = Geo<S>::LM;
   constexpr int P = Q / 2;    // ops per load instruction
   constexpr int G = 4 * P;    // ops per group
-  constexpr int NG = 32 / G;  // groups per warp
   constexpr unsigned GM = (1u << G) - 1u;
   constexpr unsigned PM = (2 * L >= 32) ? 0xFFFFFFFFu : ((1u << (2 * L)) - 1u);
   const int q = lane / L;
   const int ql = lane % L;
   const int my_g = lane / G, my_j = lane % G, my_u = my_j / P, my_p = my_j % P;
 #pragma unroll 1
-  for (int g = 0; g < NG; ++g) {
+  for (int g = o0 / G; g < o1 / G; ++g) {
     const unsigned gneed = (need >> (G * g)) & GM;
     if (!gneed) continue;
     uint64_t wa[4], wb[4];
@@ -370,15 +523,25 @@ __device__ __forceinline__ void probe_pair(const View& v, unsigned need, uint32_
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int src = G * g + P * u + (q >> 1);
-      const uint32_t q1 = __shfl_sync(kFull, b1, src);
-      const uint32_t q2 = __shfl_sync(kFull, b2, src);
-      kq[u] = __shfl_sync(kFull, key, src);
-      if ((gneed >> (P * u + (q >> 1))) & 1u) {
-        const uint64_t* p = v.buckets + static_cast<uint64_t>((q & 1) ? q2 : q1) * S + 2 * ql;
-        ld_frag(p, wa[u], wb[u]);
+      if (STAGED) {
+        kq[u] = __shfl_sync(kFull, key, src);
+        if ((gneed >> (P * u + (q >> 1))) & 1u) {
+          lds_frag(sbuf + (2 * (src - o0) + (q & 1)) * S + 2 * ql, wa[u], wb[u]);
+        } else {
+          wa[u] = kEmptyWord;
+          wb[u] = kEmptyWord;
+        }
       } else {
-        wa[u] = kEmptyWord;
-        wb[u] = kEmptyWord;
+        const uint32_t q1 = __shfl_sync(kFull, b1, src);
+        const uint32_t q2 = __shfl_sync(kFull, b2, src);
+        kq[u] = __shfl_sync(kFull, key, src);
+        if ((gneed >> (P * u + (q >> 1))) & 1u) {
+          const uint64_t* p = v.buckets + static_cast<uint64_t>((q & 1) ? q2 : q1) * S + 2 * ql;
+          ld_frag(p, wa[u], wb[u]);
+        } else {
+          wa[u] = kEmptyWord;
+          wb[u] = kEmptyWord;
+        }
       }
     }
     unsigned my_m = 0, my_mh = 0, my_el = 0, my_eh = 0;
@@ -419,18 +582,62 @@ __device__ __forceinline__ void probe_pair(const View& v, unsigned need, uint32_
         else
           cnt.contract = true;
       } else {
-        const unsigned e0 = (my_el >> base) & LM, o0 = (my_eh >> base) & LM;
-        const unsigned e1 = (my_el >> (base + L)) & LM, o1 = (my_eh >> (base + L)) & LM;
-        f1 = __popc(e0) + __popc(o0);
-        f2 = __popc(e1) + __popc(o1);
+        const unsigned e0 = (my_el >> base) & LM, o_0 = (my_eh >> base) & LM;
+        const unsigned e1 = (my_el >> (base + L)) & LM, o_1 = (my_eh >> (base + L)) & LM;
+        f1 = __popc(e0) + __popc(o_0);
+        f2 = __popc(e1) + __popc(o_1);
         const uint32_t a0 = e0 ? 2u * (__ffs(e0) - 1) : S;
-        const uint32_t a1 = o0 ? 2u * (__ffs(o0) - 1) + 1u : S;
+        const uint32_t a1 = o_0 ? 2u * (__ffs(o_0) - 1) + 1u : S;
         const uint32_t c0 = e1 ? 2u * (__ffs(e1) - 1) : S;
-        const uint32_t c1 = o1 ? 2u * (__ffs(o1) - 1) + 1u : S;
+        const uint32_t c1 = o_1 ? 2u * (__ffs(o_1) - 1) + 1u : S;
         s1 = a0 < a1 ? a0 : a1;
         s2 = c0 < c1 ? c0 : c1;
       }
     }
+  }
+}
+
+// A single-bucket probe round, staged when the warp has a live stage.
+template <int MODE, int S>
+__device__ __forceinline__ void probe_round(const View& v, unsigned need, uint32_t myb,
+                                            uint32_t key, uint32_t val, uint32_t op, int lane,
+                                            bool& done, uint8_t& st, uint32_t& outv,
+                                            uint32_t& fcnt, uint32_t& fslot, LaneCounters& cnt,
+                                            Stage* sg) {
+  if (sg && !sg->dead && stage_round<S, false>(v, *sg, need, 0, myb, 0, lane))
+    probe<MODE, S, true>(v, need, myb, key, val, op, lane, done, st, outv, fcnt, fslot, cnt,
+                         sg->buf);
+  else
+    probe<MODE, S, false>(v, need, myb, key, val, op, lane, done, st, outv, fcnt, fslot, cnt,
+                          nullptr);
+}
+
+// The paired insert round, staged in batches of 512 / S ops when the warp has
+// a live stage.
+template <int S>
+__device__ __forceinline__ void probe_pair_round(const View& v, unsigned need, uint32_t b1,
+                                                 uint32_t b2, uint32_t key, uint32_t val,
+                                                 int lane, bool& done, uint8_t& st, uint32_t& f1,
+                                                 uint32_t& s1, uint32_t& f2, uint32_t& s2,
+                                                 LaneCounters& cnt, Stage* sg) {
+  constexpr int BO = kStageWords / (2 * S);
+  constexpr unsigned BM = (BO >= 32) ? 0xFFFFFFFFu : ((1u << BO) - 1u);
+  if (sg) {
+#pragma unroll 1
+    for (int o0 = 0; o0 < 32; o0 += BO) {
+      const unsigned bneed = need & (BM << o0);
+      if (!bneed) continue;
+      if (sg->dead || !stage_round<S, true>(v, *sg, bneed, o0, b1, b2, lane)) {
+        probe_pair<S, false>(v, need & ~((1u << o0) - 1u), b1, b2, key, val, lane, done, st, f1,
+                             s1, f2, s2, cnt, nullptr, o0, 32);
+        return;
+      }
+      probe_pair<S, true>(v, bneed, b1, b2, key, val, lane, done, st, f1, s1, f2, s2, cnt,
+                          sg->buf, o0, o0 + BO);
+    }
+  } else {
+    probe_pair<S, false>(v, need, b1, b2, key, val, lane, done, st, f1, s1, f2, s2, cnt, nullptr,
+                         0, 32);
   }
 }
 
@@ -473,7 +680,7 @@ __device__ __forceinline__ void flush_counters(const View& v, LaneCounters& cnt,
 template <int MODE, int S>
 __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const OpPtrs a,
                                           uint32_t c, uint64_t n, const List ovf, uint32_t seg,
-                                          LaneCounters& cnt, int lane) {
+                                          LaneCounters& cnt, int lane, Stage* sg = nullptr) {
   constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
   const uint32_t i = (c << 5) + lane;
   const bool valid = i < n;
@@ -504,13 +711,13 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
   unsigned need = __ballot_sync(kFull, !done);
   if (MODE == kModeInsert) {
     cnt.probes += 2 * __popc(need);
-    if (need) probe_pair<S>(v, need, b1, b2, key, val, lane, done, st, f1, s1, f2, s2, cnt);
+    if (need) probe_pair_round<S>(v, need, b1, b2, key, val, lane, done, st, f1, s1, f2, s2, cnt, sg);
   } else {
     cnt.probes += __popc(need);
-    if (need) probe<MODE, S>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt);
+    if (need) probe_round<MODE, S>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt, sg);
     need = __ballot_sync(kFull, !done);
     cnt.probes += __popc(need);
-    if (need) probe<MODE, S>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt);
+    if (need) probe_round<MODE, S>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt, sg);
   }
 
   // The stash (Section IV-A step 4) holds keys that found no bucket room.
@@ -593,7 +800,9 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
 }
 
 template <int MODE, int S>
-__global__ void __launch_bounds__(kOpsThreads, HIVE_OPS_MIN_BLOCKS)
+__global__ void __launch_bounds__(kOpsThreads, ((HIVE_STAGED_MODES >> MODE) & 1)
+                                                   ? HIVE_STAGED_MIN_BLOCKS
+                                                   : HIVE_OPS_MIN_BLOCKS)
     k_ops(View v, OpPtrs a, uint64_t n, List ovf) {
   const int lane = threadIdx.x & 31;
   // n < 2^32 per call, so chunk and op indices fit 32 bits
@@ -602,8 +811,17 @@ __global__ void __launch_bounds__(kOpsThreads, HIVE_OPS_MIN_BLOCKS)
   const uint32_t nchunks = static_cast<uint32_t>((n + 31) >> 5);
   const uint32_t stash_n = v.ctrl->stash_n;
   LaneCounters cnt;
-  for (uint32_t c = warp0; c < nchunks; c += nwarps)
-    run_chunk<MODE, S>(v, stash_n, a, c, n, ovf, 0, cnt, lane);
+  if ((HIVE_STAGED_MODES >> MODE) & 1) {
+    // bucket reads staged in shared memory by bulk copies
+    extern __shared__ __align__(16) uint64_t ops_smem[];
+    Stage sg = stage_init(ops_smem, threadIdx.x >> 5, lane);
+    for (uint32_t c = warp0; c < nchunks; c += nwarps)
+      run_chunk<MODE, S>(v, stash_n, a, c, n, ovf, 0, cnt, lane, &sg);
+    stage_drain(sg);
+  } else {
+    for (uint32_t c = warp0; c < nchunks; c += nwarps)
+      run_chunk<MODE, S>(v, stash_n, a, c, n, ovf, 0, cnt, lane);
+  }
   flush_counters(v, cnt, lane);
 }
 
@@ -1156,11 +1374,14 @@ cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys
   const uint64_t chunks = (n + 31) / 32;
   const uint64_t warps_per_block = kOpsThreads / 32;
   uint64_t blocks = (chunks + warps_per_block - 1) / warps_per_block;
-  const uint64_t cap = static_cast<uint64_t>(L.num_sms) * L.ops_blocks_per_sm;
+  constexpr bool kStaged = (HIVE_STAGED_MODES >> MODE) & 1;
+  const int per_sm = kStaged ? L.staged_blocks_per_sm : L.ops_blocks_per_sm;
+  const uint64_t cap = static_cast<uint64_t>(L.num_sms) * per_sm;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   const OpPtrs a{ops, keys, vals, vals_out, found, status};
-  k_ops<MODE, S><<<static_cast<unsigned>(blocks), kOpsThreads, 0, s>>>(v, a, n, ovf);
+  const size_t smem = kStaged ? kStageSmemBytes : 0;
+  k_ops<MODE, S><<<static_cast<unsigned>(blocks), kOpsThreads, smem, s>>>(v, a, n, ovf);
   return cudaGetLastError();
 }
 
@@ -1309,10 +1530,23 @@ namespace {
 template <int S>
 cudaError_t occupancy_s(Launch* L) {
   int b = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeInsert, S>,
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeFind, S>,
                                                                 kOpsThreads, 0);
   if (e != cudaSuccess) return e;
   L->ops_blocks_per_sm = b > 0 ? b : 1;
+  const int stage_smem = static_cast<int>(kStageSmemBytes);
+  e = cudaFuncSetAttribute(k_ops<kModeFind, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ops<kModeInsert, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ops<kModeErase, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ops<kModeMixed, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage_smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeInsert, S>, kOpsThreads,
+                                                    kStageSmemBytes);
+  if (e != cudaSuccess) return e;
+  L->staged_blocks_per_sm = b > 0 ? b : 1;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_multi_ops<S>, kOpsThreads, 0);
   if (e != cudaSuccess) return e;
   L->multi_blocks_per_sm = b > 0 ? b : 1;

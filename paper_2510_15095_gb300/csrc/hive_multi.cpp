@@ -290,6 +290,10 @@ hive_status hive_multi_execute(hive_multi* m, const hive_segment* segs, uint32_t
       if (st != HIVE_OK) return st;
     }
   }
+  for (uint32_t t : touched) {  // back the buckets the split waves create
+    hive_status st = ensure_committed(m->tables[t], s);
+    if (st != HIVE_OK) return st;
+  }
   for (auto& w : waves) {
     m->wave_begin.push_back(static_cast<uint32_t>(m->jobs.size()));
     uint32_t pair0 = 0;

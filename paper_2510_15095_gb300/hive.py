@@ -32,7 +32,7 @@ EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", 
            "hive_stats", "hive_dump", "hive_profile_enable", "hive_profile_read",
            "hive_insert_noalloc", "hive_multi_create", "hive_multi_execute",
            "hive_multi_destroy", "hive_insert_host", "hive_find_host", "hive_execute_host",
-           "hive_reserve", "hive_last_error"]
+           "hive_reserve", "hive_memory", "hive_last_error"]
 KERNEL_KINDS = ["find", "insert", "erase", "mixed", "evict", "maint", "split", "merge", "count"]
 
 
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH):
         L.hive_size.argtypes = [vp, C.POINTER(u64), vp]
         L.hive_capacity.argtypes = [vp, C.POINTER(u64)]
         L.hive_reserve.argtypes = [vp, u64, vp]
+        L.hive_memory.argtypes = [vp, C.POINTER(u64), C.POINTER(u64)]
         L.hive_clear.argtypes = [vp, vp]
         L.hive_check.argtypes = [vp, vp]
         L.hive_stats.argtypes = [vp, C.POINTER(Stats), vp]
@@ -316,6 +317,12 @@ class HiveTable:
     def reserve(self, slots: int, stream=None):
         """Grow (resizable tables) to at least `slots` slots ahead of time."""
         _raise(self._L, self._L.hive_reserve(self._h, int(slots), _stream_ptr(stream)))
+
+    def memory(self) -> tuple:
+        """(committed, reserved) device bytes of the table."""
+        a, b = C.c_uint64(), C.c_uint64()
+        _raise(self._L, self._L.hive_memory(self._h, C.byref(a), C.byref(b)))
+        return int(a.value), int(b.value)
 
     def capacity(self) -> int:
         out = C.c_uint64()

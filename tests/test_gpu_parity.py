@@ -309,3 +309,33 @@ def test_host_buffer_calls_match_device_calls(H):
     assert a.size() == b.size()
     a.close()
     b.close()
+
+
+def test_resizable_memory_follows_capacity(H):
+    """A resizable table maps bucket memory as it splits and returns it after
+    merges: committed bucket bytes grow and shrink with the capacity inside a
+    bucket range reserved once for max_slots.  (The per-batch work lists grow
+    with the largest batch seen, on both counts.)"""
+    t = H.HiveTable(1 << 12, max_slots=1 << 24, resizable=True, resize_batch=1024)
+    c0, r0 = t.memory()
+    keys, _ = W.take_keys(55, 0, 1 << 21)
+    vals = W.values_for(keys, 55)
+    t.insert(up(H, keys), up(H, vals))
+    c1, r1 = t.memory()
+    # at least 2^21 keys worth of the reserved bucket range got mapped
+    assert (r0 - c0) - (r1 - c1) >= 16 * (1 << 20), (c0, r0, c1, r1)
+    d = oracle.Dict()
+    d.insert(keys, vals)
+    check_find(H, t, d, keys[::7])
+    t.erase(up(H, keys[: (1 << 21) - (1 << 14)]))
+    d.erase(keys[: (1 << 21) - (1 << 14)])
+    c2, r2 = t.memory()
+    assert r2 == r1 and c2 < c1 - 12 * (1 << 20), (c0, c1, c2)  # the bucket memory went back
+    check_find(H, t, d, keys[::7])
+    check_image(t, d)
+    # grows again into freshly mapped, freshly emptied memory
+    t.insert(up(H, keys[: 1 << 20]), up(H, vals[: 1 << 20]))
+    d.insert(keys[: 1 << 20], vals[: 1 << 20])
+    check_find(H, t, d, keys[::5])
+    check_image(t, d)
+    t.close()
