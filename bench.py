@@ -58,6 +58,10 @@ def parse_args():
     ap.add_argument("--no-tables", action="store_true", help="skip the multi-table leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-resize", action="store_true", help="skip the resize-stream leg")
+    ap.add_argument("--bucket-slots", type=int, choices=[16, 32], default=0,
+                    help="fix the bucket width instead of autotuning it (profiling runs)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the load-factor sweep and the L2-resident small-table leg")
     ap.add_argument("--resize-batches", type=int, default=32)
     ap.add_argument("--tables-n", type=int, default=1024)
     ap.add_argument("--tables-steps", type=int, default=8)
@@ -323,6 +327,140 @@ def tables_leg(torch, H, dev, n_tables=1024, steps=8, seed=40):
 
 
 # ---------------------------------------------------------------------------
+# load-factor sweep and the L2-resident small table
+# ---------------------------------------------------------------------------
+
+def _valid_keys_t(torch, W, seed, pos0, n, dev):
+    """The first n keys of stream `seed` from position pos0 on that are not
+    reserved (0, 0xFFFFFFFE, 0xFFFFFFFF), as int64 tensors in [1, 2^32 - 3]."""
+    pos = torch.arange(pos0, pos0 + n + 64, device=dev, dtype=torch.int64)
+    k = W.feistel_bits_t(pos, seed, 32)
+    k = k[(k >= 1) & (k <= 0xFFFFFFFD)][:n]
+    assert k.numel() == n
+    return k
+
+
+def _i32(torch, t):
+    return (t - ((t >> 31) << 32)).to(torch.int32)
+
+
+def _median_ms(torch, stream, dev, fn, reps, setup=None):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = []
+    for _ in range(reps):
+        if setup is not None:
+            setup()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        out.append(e0.elapsed_time(e1))
+    return float(np.median(out))
+
+
+def sweep_leg(torch, H, dev, table_kw, slots=SLOTS, n_find=N_FIND, seed=70, reps=3):
+    """Load-factor sweep on a fixed table of `slots` slots (the paper's
+    insert/find experiment over load factors): fresh bulk fills to 50/80/90/95%
+    load, the incremental fill from 90% to 95%, and n_find finds at 50% hit at
+    each load, with hits and misses drawn uniformly or Zipf(0.99) over ranks."""
+    from paper_2510_15095_gb300 import workload as W
+    stream = torch.cuda.current_stream(dev)
+    loads = (50, 80, 90, 95)
+    n_at = {L: (slots * L * 2 + 100) // 200 for L in loads}
+    k = _valid_keys_t(torch, W, seed, 0, n_at[95], dev)
+    v = W.splitmix32_t(k ^ seed)
+    a = _valid_keys_t(torch, W, seed, 1 << 31, n_find, dev)  # never inserted
+    k32, v32, a32 = _i32(torch, k), _i32(torch, v), _i32(torch, a)
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    hit = torch.rand(n_find, generator=g, device=dev) < 0.5
+    st = torch.empty(n_at[95], dtype=torch.uint8, device=dev)
+    fv = torch.empty(n_find, dtype=torch.int32, device=dev)
+    ff = torch.empty(n_find, dtype=torch.uint8, device=dev)
+    t = H.HiveTable(slots, **table_kw)
+    S = int(table_kw.get("bucket_slots", 32))
+    out = {"workload": (f"fixed table of {slots} slots; fresh fills to 50/80/90/95% load and the "
+                        f"90->95% fill; {n_find} finds at 50% hit, uniform and Zipf(0.99) over ranks"),
+           "table": dict(table_kw), "loads": {}}
+    for L in loads:
+        n = n_at[L]
+        ins_ms = _median_ms(torch, stream, dev, lambda: t.insert(k32[:n], v32[:n], status=st[:n]),
+                            reps, setup=t.clear)
+        assert bool((st[:n] == H.INSERTED).all()) and t.check() == 0
+        row = {"n_insert": n, "insert_gops": n / ins_ms / 1e6, "insert_ms": ins_ms}
+        for dist_name in ("uniform", "zipf"):
+            if dist_name == "uniform":
+                hi = torch.randint(0, n, (n_find,), generator=g, device=dev)
+                mi = torch.randint(0, n_find, (n_find,), generator=g, device=dev)
+            else:
+                hi = W.zipf_ranks_t(torch, n, 0.99, n_find, g, dev) - 1
+                mi = W.zipf_ranks_t(torch, min(n, n_find), 0.99, n_find, g, dev) - 1
+            q = torch.where(hit, k32[hi], a32[mi])
+            before = t.stats()["probes"]
+            t.find(q, vals_out=fv, found=ff)
+            probes = (t.stats()["probes"] - before) / n_find
+            f_ms = _median_ms(torch, stream, dev, lambda: t.find(q, vals_out=fv, found=ff), reps)
+            assert bool(((ff == 1) == hit).all())
+            assert bool((fv[hit] == v32[hi[hit]]).all())
+            row[f"find_{dist_name}_gops"] = n_find / f_ms / 1e6
+            row[f"find_{dist_name}_probes"] = probes
+            row[f"find_{dist_name}_algorithmic_gbs"] = n_find * (9 + 8 * S * probes) / f_ms / 1e6
+        out["loads"][str(L)] = row
+    n90, n95 = n_at[90], n_at[95]
+    inc_ms = _median_ms(torch, stream, dev,
+                        lambda: t.insert(k32[n90:n95], v32[n90:n95], status=st[n90:n95]), reps,
+                        setup=lambda: (t.clear(), t.insert(k32[:n90], v32[:n90], status=False)))
+    assert bool((st[n90:n95] == H.INSERTED).all()) and t.check() == 0
+    out["incremental_90_95"] = {"n_insert": n95 - n90, "insert_gops": (n95 - n90) / inc_ms / 1e6,
+                                "insert_ms": inc_ms}
+    t.close()
+    return out
+
+
+def plain_leg(torch, H, dev, seed=80, reps=5):
+    """The small plain table (2^20 slots, 8 MiB, resident in the 129 MB L2):
+    insert 838,861 keys (80%), 1,677,722 finds (half absent), erase a seeded
+    half of the keys, the same finds again.  Throughput here is bounded by L2
+    and launch latency, not HBM."""
+    from paper_2510_15095_gb300 import workload as W
+    stream = torch.cuda.current_stream(dev)
+    slots, n_ins, n_find = 1 << 20, 838861, 1677722
+    k = _valid_keys_t(torch, W, seed, 0, n_ins, dev)
+    v = W.splitmix32_t(k ^ seed)
+    a = _valid_keys_t(torch, W, seed, 1 << 31, n_find, dev)
+    k32, v32, a32 = _i32(torch, k), _i32(torch, v), _i32(torch, a)
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    hit = torch.rand(n_find, generator=g, device=dev) < 0.5
+    q = torch.where(hit, k32[torch.randint(0, n_ins, (n_find,), generator=g, device=dev)],
+                    a32[torch.randint(0, n_find, (n_find,), generator=g, device=dev)])
+    er = k32[torch.randperm(n_ins, generator=g, device=dev)[: n_ins // 2]]
+    t = H.HiveTable(slots)
+    st = torch.empty(n_ins, dtype=torch.uint8, device=dev)
+    fv = torch.empty(n_find, dtype=torch.int32, device=dev)
+    ff = torch.empty(n_find, dtype=torch.uint8, device=dev)
+    es = torch.empty(n_ins // 2, dtype=torch.uint8, device=dev)
+    ins_ms = _median_ms(torch, stream, dev, lambda: t.insert(k32, v32, status=st), reps, setup=t.clear)
+    f1_ms = _median_ms(torch, stream, dev, lambda: t.find(q, vals_out=fv, found=ff), reps)
+    assert bool(((ff == 1) == hit).all())
+
+    def restore():
+        t.clear()
+        t.insert(k32, v32, status=False)
+    er_ms = _median_ms(torch, stream, dev, lambda: t.erase(er, status=es), reps, setup=restore)
+    assert bool((es == H.ERASED).all())
+    f2_ms = _median_ms(torch, stream, dev, lambda: t.find(q, vals_out=fv, found=ff), reps)
+    assert t.size() == n_ins - n_ins // 2 and t.check() == 0
+    t.close()
+    return {"workload": ("fixed table of 2^20 slots (L2-resident): insert 838,861, find 1,677,722 "
+                         "(half absent), erase 419,430, find again"),
+            "insert_gops": n_ins / ins_ms / 1e6, "find_gops": n_find / f1_ms / 1e6,
+            "erase_gops": (n_ins // 2) / er_ms / 1e6, "find_after_erase_gops": n_find / f2_ms / 1e6,
+            "ms": {"insert": ins_ms, "find": f1_ms, "erase": er_ms, "find_after_erase": f2_ms}}
+
+
+# ---------------------------------------------------------------------------
 # resize-stream leg: one table grows and shrinks through linear hashing
 # ---------------------------------------------------------------------------
 
@@ -512,7 +650,10 @@ def main():
     # bucket width and knobs from the autotuner for this workload class (the
     # paper's default S = 32 is measured too, below)
     from paper_2510_15095_gb300 import autotune as AT
-    tuned = AT.tune(args.slots, 95, (1, 2, 1), False, space=BENCH_SPACE)
+    if args.bucket_slots:
+        tuned = {"bucket_slots": args.bucket_slots, "max_evictions": 16, "placement": 0}
+    else:
+        tuned = AT.tune(args.slots, 95, (1, 2, 1), False, space=BENCH_SPACE)
     cfg["table"] = dict(tuned)
     t = H.HiveTable(args.slots, **tuned)
     stream = torch.cuda.current_stream(dev)
@@ -707,6 +848,10 @@ def main():
         extra["serving"] = serving_leg(torch, H, dev, n_requests=args.serving_requests)
     if not args.no_resize:
         extra["resize_stream"] = resize_leg(torch, H, dev, batches=args.resize_batches)
+    if not args.no_sweep:
+        extra["load_sweep"] = sweep_leg(torch, H, dev, tuned, slots=args.slots,
+                                        n_find=N_FIND if args.slots == SLOTS else args.slots)
+        extra["plain_2e20"] = plain_leg(torch, H, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
