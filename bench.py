@@ -327,6 +327,105 @@ def tables_leg(torch, H, dev, n_tables=1024, steps=8, seed=40):
 
 
 # ---------------------------------------------------------------------------
+# single-kernel mixed batches against the phased launches
+# ---------------------------------------------------------------------------
+
+def fused_leg(torch, H, dev, t, ik, iv, mo, mk, mv, reps=3, small=4096, n_small=256):
+    """The bench's mixed batch at 95% load run as one concurrent kernel
+    (hive_execute_fused) and as the phased launches (hive_execute): whole
+    batch, and as `n_small` consecutive slices of `small` ops (latency-bound
+    small batches).  Results must be identical."""
+    stream = torch.cuda.current_stream(dev)
+
+    def restore():
+        t.clear()
+        t.insert(ik, iv, status=False)
+
+    out = {"workload": (f"mixed batch of {mo.numel()} ops (insert:find:erase 1:2:1) at 95% load, "
+                        f"whole and as {n_small} slices of {small} ops")}
+    res = {}
+    for name, fused in (("phased", False), ("fused", True)):
+        restore()
+        res[name] = t.execute(mo, mk, mv, fused=fused)
+        ms = _median_ms(torch, stream, dev, lambda: t.execute(mo, mk, mv, fused=fused), reps,
+                        setup=restore)
+        out[f"{name}_gops"] = mo.numel() / ms / 1e6
+        out[f"{name}_ms"] = ms
+        m = min(n_small * small, mo.numel())
+
+        def slices():
+            for j in range(0, m, small):
+                t.execute(mo[j:j + small], mk[j:j + small], mv[j:j + small], fused=fused)
+        ms_s = _median_ms(torch, stream, dev, slices, reps, setup=restore)
+        out[f"{name}_small_batch_us"] = ms_s * 1e3 / (m // small)
+        out[f"{name}_small_gops"] = m / ms_s / 1e6
+    out["identical_results"] = bool(torch.equal(res["phased"][0], res["fused"][0]) and
+                                    torch.equal(res["phased"][1], res["fused"][1]))
+    assert out["identical_results"], "fused and phased mixed batches disagree"
+    restore()
+    before = t.stats()["fused_retries"]
+    t.execute(mo, mk, mv, fused=True)
+    out["lookup_retries"] = t.stats()["fused_retries"] - before
+    return out
+
+
+# ---------------------------------------------------------------------------
+# 32-bit entries: a key-only set with 128-byte buckets
+# ---------------------------------------------------------------------------
+
+def hive32_leg(torch, H, dev, slots=SLOTS, n_find=N_FIND, seed=90, reps=3):
+    """The load-factor-sweep table with 32-bit entries (a set of 32-bit keys,
+    32 slots per 128-byte bucket): bulk insert to 95% load, n_find finds at 50%
+    hit, and a mixed batch of slots / 4 ops (insert:find:erase 1:2:1)."""
+    from paper_2510_15095_gb300 import workload as W
+    stream = torch.cuda.current_stream(dev)
+    n = (slots * 19 * 2 + 20) // 40
+    k32 = _i32(torch, _valid_keys_t(torch, W, seed, 0, n, dev))
+    a32 = _i32(torch, _valid_keys_t(torch, W, seed, 1 << 31, n_find, dev))
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    hit = torch.rand(n_find, generator=g, device=dev) < 0.5
+    q = torch.where(hit, k32[torch.randint(0, n, (n_find,), generator=g, device=dev)],
+                    a32[torch.randint(0, n_find, (n_find,), generator=g, device=dev)])
+    n_mix = slots // 4
+    perm = torch.randperm(n, generator=g, device=dev)
+    new = _i32(torch, _valid_keys_t(torch, W, seed, 1 << 30, n_mix // 4, dev))
+    keys_m = torch.cat([new, k32[perm[: n_mix // 4]], k32[perm[n_mix // 4: n_mix // 4 + n_mix // 2]]])
+    ops_m = torch.cat([torch.zeros(n_mix // 4, dtype=torch.uint8, device=dev),
+                       torch.full((n_mix // 4,), 2, dtype=torch.uint8, device=dev),
+                       torch.ones(n_mix // 2, dtype=torch.uint8, device=dev)])
+    order = torch.randperm(keys_m.numel(), generator=g, device=dev)
+    keys_m, ops_m = keys_m[order].contiguous(), ops_m[order].contiguous()
+    t = H.Hive32Table(slots, H.KEY_ONLY)
+    st = torch.empty(n, dtype=torch.uint8, device=dev)
+    fv = torch.empty(n_find, dtype=torch.int32, device=dev)
+    ff = torch.empty(n_find, dtype=torch.uint8, device=dev)
+    ins_ms = _median_ms(torch, stream, dev, lambda: t.insert(k32, status=st), reps, setup=t.clear)
+    assert bool((st == H.INSERTED).all()) and t.check() == 0
+    s0 = t.stats()["probes"]
+    t.find(q, vals_out=fv, found=ff)
+    probes = (t.stats()["probes"] - s0) / n_find
+    f_ms = _median_ms(torch, stream, dev, lambda: t.find(q, vals_out=fv, found=ff), reps)
+    assert bool(((ff == 1) == hit).all())
+
+    def restore():
+        t.clear()
+        t.insert(k32, status=False)
+    m_ms = _median_ms(torch, stream, dev, lambda: t.execute(ops_m, keys_m), reps, setup=restore)
+    assert t.check() == 0
+    t.close()
+    return {"workload": (f"fixed table of {slots} slots with 32-bit entries (key-only set, 128-byte "
+                         f"buckets): insert {n} keys (95% load), {n_find} finds at 50% hit, mixed "
+                         f"batch of {n_mix} ops 1:2:1"),
+            "insert_gops": n / ins_ms / 1e6, "find_gops": n_find / f_ms / 1e6,
+            "mixed_gops": n_mix / m_ms / 1e6, "probes_per_find": probes,
+            # key in, value + flag out, 128 bytes per probed bucket
+            "find_algorithmic_gbs": n_find * (9 + 128 * probes) / f_ms / 1e6,
+            "insert_algorithmic_gbs": n * (4 + 1 + 2 * 128 + 32) / ins_ms / 1e6,
+            "ms": {"insert": ins_ms, "find": f_ms, "mixed": m_ms}}
+
+
+# ---------------------------------------------------------------------------
 # load-factor sweep and the L2-resident small table
 # ---------------------------------------------------------------------------
 
@@ -783,6 +882,8 @@ def main():
                        "step_gops": ops_step / (a.sum() + 0.0) / 1e6}
         t32.close()
 
+    fused = fused_leg(torch, H, dev, t, ik, iv, mo, mk, mv)
+
     ph = np.array(phase_ms)
     phases = {"insert_gops": n_ins / (ph[:, 0].mean() / 1e3) / 1e9,
               "find_gops": n_find / (ph[:, 1].mean() / 1e3) / 1e9,
@@ -793,7 +894,7 @@ def main():
               "probes_per_find": probes_find / n_find, "probes_per_insert": probes_ins / n_ins,
               "probes_per_mixed": probes_mix / n_mix,
               "insert_overflowed": overflowed, "insert_stashed": stashed,
-              "paper_default_s32": default_s32}
+              "paper_default_s32": default_s32, "fused_mixed": fused}
 
     # end to end through the public API with host buffers: the host-buffer
     # calls stream pinned host arrays through device staging, overlapping the
@@ -852,6 +953,8 @@ def main():
         extra["load_sweep"] = sweep_leg(torch, H, dev, tuned, slots=args.slots,
                                         n_find=N_FIND if args.slots == SLOTS else args.slots)
         extra["plain_2e20"] = plain_leg(torch, H, dev)
+        extra["hive32_key_only"] = hive32_leg(torch, H, dev, slots=args.slots,
+                                              n_find=N_FIND if args.slots == SLOTS else args.slots)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -117,6 +117,8 @@ typedef struct {
   uint64_t probes;           /* 256-byte bucket reads by the bulk kernel (Section IV-B:
                                 one per candidate bucket examined) */
   uint64_t stash_lookups;    /* binary searches of the stash by the bulk kernel */
+  uint64_t fused_retries;    /* single-kernel batches: lookups repeated because a
+                                candidate bucket had a word in transit */
 } hive_stats_t;
 
 /* Kernel kinds timed by the profiling hook. */
@@ -130,6 +132,7 @@ enum {
   HIVE_K_SPLIT = 6,    /* linear-hashing split */
   HIVE_K_MERGE = 7,    /* linear-hashing merge and its pre-check */
   HIVE_K_COUNT = 8,    /* insert counting for a resizable mixed batch */
+  HIVE_K_FUSED = 9,    /* single-kernel mixed batch (hive_execute_fused) */
   HIVE_K_KINDS = 16
 };
 
@@ -193,6 +196,23 @@ hive_status hive_erase(hive_table* t, const uint32_t* keys, uint64_t n, uint8_t*
 hive_status hive_execute(hive_table* t, const uint8_t* ops, const uint32_t* keys,
                          const uint32_t* vals, uint64_t n, uint32_t* vals_out,
                          uint8_t* status, void* stream);
+
+/* The same mixed batch in one kernel, the paper's single-kernel mode
+ * (Section III-D: all operation types of a batch run concurrently in one
+ * launch).  Finds, erases, replaces, claims, cuckoo eviction chains
+ * (Algorithm 3) and stash appends of the batch all run at once.  A lookup
+ * that misses while a chain is moving a word out of one of its candidate
+ * buckets is repeated: each bucket carries a version word that chains raise
+ * and lower around the move, and a miss counts only if both versions were
+ * quiet and unchanged across the probe.  Arguments, per-op results, the batch
+ * contract and the errors are exactly those of hive_execute(), and so are
+ * the results.  A resizable table grows before the kernel as in
+ * hive_execute(); inserts that still find no room (stash full) are placed
+ * after further growth by the eviction kernel, before the call returns.
+ * Stash maintenance follows as a second, usually empty, launch. */
+hive_status hive_execute_fused(hive_table* t, const uint8_t* ops, const uint32_t* keys,
+                               const uint32_t* vals, uint64_t n, uint32_t* vals_out,
+                               uint8_t* status, void* stream);
 
 /* Live entries (buckets + stash).  Synchronises `stream`. */
 hive_status hive_size(hive_table* t, uint64_t* out, void* stream);
@@ -329,6 +349,76 @@ hive_status hive_multi_destroy(hive_multi* m);
  *    two streams at once) race and must not be issued. */
 hive_status hive_insert_noalloc(hive_table* t, const uint32_t* keys, const uint32_t* vals,
                                 uint64_t n, uint8_t* status, void* stream);
+
+/* ---- Tables with 32-bit entries ----
+ * Section III-B: with 32-bit entries (a key-only set, or a 16-bit key and a
+ * 16-bit value) a bucket of 32 slots fits one 128-byte cache line, half the
+ * bytes of a probe of the 64-bit table.  Same algorithm (replace, claim,
+ * bounded cuckoo eviction, stash; match-and-elect lookups), fixed capacity,
+ * 32 slots per bucket, BitHash1/BitHash2 of the (16- or 32-bit) key.  Same
+ * conventions as the calls above: device op arrays owned by the caller,
+ * stream-ordered, the batch contract, per-op status codes, sticky errors.
+ *  - HIVE32_KEY16_VAL16: entry = value << 16 | key.  Keys must be below
+ *    0xFFFE and values below 2^16; an op whose key (or, for an insert, value)
+ *    is out of range reports HIVE_ST_RESERVED_KEY and raises
+ *    HIVE_ERR_RESERVED_KEY.  Finds return the 16-bit value.
+ *  - HIVE32_KEY_ONLY: entry = key, a set of 32-bit keys (0xFFFFFFFE and
+ *    0xFFFFFFFF reserved).  vals may be NULL and is ignored; an insert of a
+ *    present key reports HIVE_ST_REPLACED; finds return value 0 and the
+ *    found flag. */
+enum { HIVE32_KEY16_VAL16 = 0, HIVE32_KEY_ONLY = 1 };
+
+typedef struct hive32_table hive32_table; /* opaque */
+
+typedef struct {
+  uint64_t slots;           /* capacity in slots, rounded up to a multiple of 32 (>= 32) */
+  uint32_t layout;          /* HIVE32_KEY16_VAL16 or HIVE32_KEY_ONLY */
+  uint32_t max_evictions;   /* cuckoo displacement bound per insert (1..64, default 16) */
+  uint32_t stash_permille;  /* stash capacity in 1/1000 of the slots (default 10; at least 1024) */
+  uint32_t lock_spin_limit; /* bounded bucket-lock wait, in tries (default 1 << 16) */
+} hive32_config;
+
+/* A host image of a quiescent 32-bit table (hive32_dump). */
+typedef struct {
+  uint64_t nb;          /* buckets = M + 1 + p */
+  uint32_t M, p;        /* linear-hashing address state (p > 0 when nb is not a power of two) */
+  uint32_t layout;
+  uint32_t* buckets;    /* [nb * 32] entries, 0xFFFFFFFF = empty (caller-allocated) */
+  uint32_t* masks;      /* [nb] free masks */
+  uint32_t* locks;      /* [nb] */
+  uint32_t* stash;      /* [stash_cap] sorted live prefix of stash_n entries */
+  uint64_t stash_n, stash_cap, size, pending;
+} hive32_image;
+
+void hive32_config_default(hive32_config* cfg);
+/* Allocates the table (buckets, masks, locks, stash) on the current device.
+ * Errors: INVALID_ARG for a bad layout or size; OOM. */
+hive_status hive32_create(const hive32_config* cfg, void* stream, hive32_table** out);
+hive_status hive32_destroy(hive32_table* t);
+/* Insert/Replace (vals may be NULL for HIVE32_KEY_ONLY); status nullable:
+ * INSERTED / REPLACED / FULL / RESERVED_KEY. */
+hive_status hive32_insert(hive32_table* t, const uint32_t* keys, const uint32_t* vals, uint64_t n,
+                          uint8_t* status, void* stream);
+/* Search: vals_out (nullable) gets the value or 0, found (nullable) 1 or 0. */
+hive_status hive32_find(hive32_table* t, const uint32_t* keys, uint64_t n, uint32_t* vals_out,
+                        uint8_t* found, void* stream);
+/* Delete: status nullable, ERASED / NOT_FOUND / RESERVED_KEY. */
+hive_status hive32_erase(hive32_table* t, const uint32_t* keys, uint64_t n, uint8_t* status,
+                         void* stream);
+/* Mixed batch of HIVE_OP_* codes, as hive_execute. */
+hive_status hive32_execute(hive32_table* t, const uint8_t* ops, const uint32_t* keys,
+                           const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* status,
+                           void* stream);
+/* Live entries; synchronises `stream`. */
+hive_status hive32_size(hive32_table* t, uint64_t* out, void* stream);
+/* Empties the table (stream-ordered; no synchronisation). */
+hive_status hive32_clear(hive32_table* t, void* stream);
+/* Returns and clears the sticky error word, as hive_check; synchronises. */
+hive_status hive32_check(hive32_table* t, void* stream);
+/* Counters (the fields of hive_stats_t that apply); synchronises. */
+hive_status hive32_stats(hive32_table* t, hive_stats_t* out, void* stream);
+/* Host image; with img->buckets == NULL only the scalar fields are filled. */
+hive_status hive32_dump(hive32_table* t, hive32_image* img, void* stream);
 
 /* Text of the calling thread's last error (never NULL). */
 const char* hive_last_error(void);

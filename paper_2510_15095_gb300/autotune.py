@@ -5,11 +5,11 @@ it times every candidate configuration on a synthetic workload of that class
 on the current GPU and caches the fastest in a JSON file.  The knobs:
 
 * bucket_slots S (Section III-B, 32 by default): 16, 32
-* max_evictions (cuckoo displacement bound, Section III-B): 8, 16, 32
+* max_evictions (cuckoo displacement bound, Section III-B): 4, 8, 16, 32
 * placement (two-choice policy): balanced, BitHash1-first
 * blocks_per_sm (persistent grid of the bulk kernel): 3, 4
 * resize_batch K (bucket pairs per split/merge launch, Section IV-C), for
-  resizable tables: 256, 1024, 4096
+  resizable tables: 256, 1024, 4096, 8192
 
 Every candidate must return the same per-op results -- the knobs change
 layout and speed only -- and the tuner checks that as it goes.
@@ -24,9 +24,9 @@ import time
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "hive_gb300", "autotune.json")
 
-FIXED_SPACE = {"bucket_slots": [16, 32], "max_evictions": [8, 16, 32], "placement": [0, 1],
+FIXED_SPACE = {"bucket_slots": [16, 32], "max_evictions": [4, 8, 16, 32], "placement": [0, 1],
                "blocks_per_sm": [3, 4]}
-RESIZE_SPACE = {"bucket_slots": [16, 32], "resize_batch": [256, 1024, 4096], "max_evictions": [16],
+RESIZE_SPACE = {"bucket_slots": [16, 32], "resize_batch": [256, 1024, 4096, 8192], "max_evictions": [16],
                 "placement": [0, 1]}
 LOAD_BANDS = (50, 80, 90, 95)
 

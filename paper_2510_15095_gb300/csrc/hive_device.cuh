@@ -1,0 +1,129 @@
+// Device helpers shared by the kernel files: per-op codes, the BitHash
+// mixes and the linear-hashing address, relaxed/acquire memory access, and
+// the bulk-copy (TMA) + mbarrier primitives used to stage bucket reads in
+// shared memory.  Everything is inline and internal to each file.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hive {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Per-op status codes (same numbers as include/hive.h).
+enum : uint8_t {
+  ST_INSERTED = 0,
+  ST_REPLACED = 1,
+  ST_ERASED = 2,
+  ST_NOT_FOUND = 3,
+  ST_FOUND = 4,
+  ST_FULL = 5,
+  ST_RESERVED = 6
+};
+enum : uint32_t { OP_INSERT = 0, OP_FIND = 1, OP_ERASE = 2 };
+
+// ----------------------------------------------------------------------------
+// Hashing and addressing
+// ----------------------------------------------------------------------------
+
+// BitHash1 (Section III-C, Listing 1) without the final reduction: a
+// Wang-style shift/xor/multiply avalanche.
+__device__ __forceinline__ uint32_t bithash1(uint32_t k) {
+  uint32_t x = (k << 15) - k - 1u;
+  x = x ^ (x >> 12);
+  x = x + (x << 2);
+  x = x ^ (x >> 4);
+  x = x * 2057u;
+  return x ^ (x >> 16);
+}
+
+// BitHash2 (Section III-C, Listing 1) without the final reduction: Jenkins'
+// six-step add/xor/shift mix.
+__device__ __forceinline__ uint32_t bithash2(uint32_t k) {
+  uint32_t x = k * 4097u + 0x7ED55D16u;
+  x = x ^ (x >> 19) ^ 0xC761C23Cu;
+  x = x * 33u + 0x165667B1u;
+  x = (x + 0xD3A2646Cu) ^ (x << 9);
+  x = x * 9u + 0xFD7046C5u;
+  return x ^ (x >> 16) ^ 0xB55A4F09u;
+}
+
+// Linear-hashing address (Section IV-C): buckets below the split pointer have
+// been split this round and use one more hash bit.
+__device__ __forceinline__ uint32_t lh_bucket(uint32_t h, uint32_t M, uint32_t p) {
+  const uint32_t b = h & M;
+  return b < p ? (h & (2u * M + 1u)) : b;
+}
+
+// ----------------------------------------------------------------------------
+// Memory access helpers
+// ----------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t ld_relaxed64(const uint64_t* p) {
+  uint64_t r;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(r) : "l"(p) : "memory");
+  return r;
+}
+__device__ __forceinline__ uint32_t ld_relaxed32(const uint32_t* p) {
+  uint32_t r;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");
+  return r;
+}
+__device__ __forceinline__ void st_relaxed64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long* ull(uint64_t* p) {
+  return reinterpret_cast<unsigned long long*>(p);
+}
+
+// ---- TMA bulk copies (cp.async.bulk) into shared memory, mbarrier-tracked ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// One bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) writes to the same memory.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void lds_frag(const uint64_t* p, uint64_t& a, uint64_t& b) {
+  asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ uint32_t ld_acquire32(const uint32_t* p) {
+  uint32_t r;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");
+  return r;
+}
+
+}  // namespace
+}  // namespace hive

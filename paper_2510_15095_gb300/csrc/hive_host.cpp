@@ -101,6 +101,7 @@ View hive::make_view(const hive_table* t) {
   v.buckets = t->buckets;
   v.masks = t->masks;
   v.locks = t->locks;
+  v.vers = t->locks + t->nb_max;
   v.stash_kv = t->stash_kv;
   v.stash_keys = t->stash_keys;
   v.ctrl = t->ctrl;
@@ -469,7 +470,7 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
   if (e == cudaSuccess && !t->vmm)
     e = cudaMalloc(&t->buckets, t->nb_max * S * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->masks, t->nb_max * sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&t->locks, t->nb_max * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&t->locks, 2 * t->nb_max * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->stash_kv, t->stash_alloc * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->stash_keys, t->stash_cap * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->ctrl, sizeof(Ctrl));
@@ -480,7 +481,7 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(t->masks, 0xFF, t->nb_max * sizeof(uint32_t), s);
   if (e == cudaSuccess && S < 32) e = launch_fill_u32(t->masks, t->nb_max, (1u << S) - 1u, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(t->locks, 0, t->nb_max * sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->locks, 0, 2 * t->nb_max * sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->stash_kv, 0xFF, t->stash_alloc * sizeof(uint64_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->ctrl, 0, sizeof(Ctrl), s);
   if (e != cudaSuccess) {
@@ -598,6 +599,32 @@ hive_status hive_execute(hive_table* t, const uint8_t* ops, const uint32_t* keys
   return HIVE_OK;
 }
 
+hive_status hive_execute_fused(hive_table* t, const uint8_t* ops, const uint32_t* keys,
+                               const uint32_t* vals, uint64_t n, uint32_t* vals_out,
+                               uint8_t* status, void* stream) {
+  hive_status st = check_table(t);
+  if (st != HIVE_OK) return st;
+  if ((st = check_n(n)) != HIVE_OK) return st;
+  if (n == 0) return HIVE_OK;
+  if (!ops || !keys) return fail(HIVE_ERR_INVALID_ARG, "ops and keys must not be NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = ensure_lists(t, n)) != HIVE_OK) return st;
+  if (t->cfg.resizable) {
+    HIVE_CK(cudaMemsetAsync(&t->ctrl->n_insert, 0, sizeof(unsigned), s));
+    HIVE_LAUNCH(t, HIVE_K_COUNT, s, launch_count_inserts(ops, n, &t->ctrl->n_insert, s));
+    if ((st = readback(t, s)) != HIVE_OK) return st;
+    if ((st = grow_for(t, t->host_ctrl->n_insert, s)) != HIVE_OK) return st;
+  }
+  // inserts that find no room at all go to list B, the pending list that
+  // finish_resizable drains
+  HIVE_LAUNCH(t, HIVE_K_FUSED, s,
+              launch_fused(make_view(t), ops, keys, vals, n, vals_out, status, list_b(t),
+                           t->cfg.resizable, t->L, s));
+  if (t->cfg.resizable) return finish_resizable(t, status, s);
+  HIVE_LAUNCH(t, HIVE_K_MAINT, s, launch_maintenance(make_view(t), s));
+  return HIVE_OK;
+}
+
 hive_status hive_size(hive_table* t, uint64_t* out, void* stream) {
   hive_status st = check_table(t);
   if (st != HIVE_OK) return st;
@@ -636,7 +663,7 @@ hive_status hive_memory(hive_table* t, uint64_t* committed, uint64_t* reserved) 
   if (!committed || !reserved) return fail(HIVE_ERR_INVALID_ARG, "outputs must not be NULL");
   const uint64_t bucket_max = t->nb_max * t->S * sizeof(uint64_t);
   const uint64_t bucket_now = t->vmm ? t->bucket_vm.committed : bucket_max;
-  const uint64_t other = t->nb_max * 2 * sizeof(uint32_t) + t->stash_alloc * sizeof(uint64_t) +
+  const uint64_t other = t->nb_max * 3 * sizeof(uint32_t) + t->stash_alloc * sizeof(uint64_t) +
                          t->stash_cap * sizeof(uint32_t) + sizeof(Ctrl) +
                          t->list_cap * (t->cfg.resizable ? 24 : 12);
   *committed = bucket_now + other;
@@ -710,6 +737,7 @@ hive_status hive_stats(hive_table* t, hive_stats_t* out, void* stream) {
   out->merges = t->merges;
   out->probes = c[kStProbes];
   out->stash_lookups = c[kStStashLookups];
+  out->fused_retries = c[kStFusedRetries];
   return HIVE_OK;
 }
 

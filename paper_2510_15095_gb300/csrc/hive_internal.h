@@ -42,6 +42,7 @@ enum : int {
   kStMerges,
   kStProbes,
   kStStashLookups,
+  kStFusedRetries,
   kNumStats = 16
 };
 
@@ -66,6 +67,7 @@ struct View {
   uint64_t* buckets;     // [nb_max * S] packed words (value << 32 | key)
   uint32_t* masks;       // [nb_max] free masks, bit i set = slot i free
   uint32_t* locks;       // [nb_max] bucket locks (eviction only)
+  uint32_t* vers;        // [nb_max] bucket versions (single-kernel batches)
   uint64_t* stash_kv;    // [stash_alloc] stash words, EMPTY padded
   uint32_t* stash_keys;  // [stash_cap] keys of the sorted prefix
   Ctrl* ctrl;
@@ -120,6 +122,7 @@ struct Launch {
   int num_sms;
   int ops_blocks_per_sm;     // bulk kernel, fragments loaded from global memory
   int staged_blocks_per_sm;  // bulk kernel, probes staged in shared memory
+  int fused_blocks_per_sm;   // single-kernel mixed batch
   int ovf_blocks_per_sm;
   int multi_blocks_per_sm;
 };
@@ -135,6 +138,9 @@ cudaError_t launch_split(const View& v_new, uint32_t src0, uint32_t count, uint3
                          cudaStream_t s);
 cudaError_t launch_merge_excess(const View& v_new, uint32_t count, cudaStream_t s);
 cudaError_t launch_merge(const View& v_new, uint32_t count, List ovf, cudaStream_t s);
+cudaError_t launch_fused(const View& v, const uint8_t* ops, const uint32_t* keys,
+                         const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* status,
+                         List pend, int resizable, const Launch& L, cudaStream_t s);
 cudaError_t launch_count_inserts(const uint8_t* ops, uint64_t n, unsigned int* out,
                                  cudaStream_t s);
 cudaError_t launch_multi_ops(int S, const MultiHdr* hdr, const MultiSeg* segs, const View* views,
@@ -149,6 +155,37 @@ cudaError_t launch_fill_u32(uint32_t* p, uint64_t n, uint32_t value, cudaStream_
 cudaError_t launch_multi_gather(const MultiHdr* hdr, const View* views, const uint32_t* touched,
                                 uint32_t max_tables, unsigned long long* out, cudaStream_t s);
 cudaError_t query_occupancy(Launch* L, int S);
+
+// ---- tables with 32-bit entries (hive32_*) ----
+struct View32 {
+  uint32_t* buckets;     // [nb * 32] entries
+  uint32_t* masks;       // [nb] free masks
+  uint32_t* locks;       // [nb] bucket locks (eviction only)
+  uint32_t* stash_kv;    // [stash_alloc] stash entries, EMPTY padded
+  uint32_t* stash_keys;  // [stash_cap] keys of the sorted prefix
+  Ctrl* ctrl;
+  uint32_t M, p, nb, stash_cap, max_evictions, lock_spin_limit;
+  int layout;            // HIVE32_KEY16_VAL16 or HIVE32_KEY_ONLY
+};
+struct Ops32 {
+  const uint8_t* ops;
+  const uint32_t* keys;
+  const uint32_t* vals;
+  uint32_t* vals_out;
+  uint8_t* found;
+  uint8_t* status;
+};
+struct List32 {
+  uint32_t* words;
+  uint32_t* idx;
+  unsigned int* count;
+};
+cudaError_t launch32_ops(int mode, const View32& v, const Ops32& a, uint64_t n, const List32& ovf,
+                         int blocks_cap, cudaStream_t s);
+cudaError_t launch32_overflow(const View32& v, const List32& in, uint8_t* status, int blocks,
+                              cudaStream_t s);
+cudaError_t launch32_maint(const View32& v, cudaStream_t s);
+cudaError_t setup32(int layout, int* blocks_per_sm);
 
 }  // namespace hive
 
@@ -193,7 +230,7 @@ struct hive_table {
   uint64_t stash_alloc = 0;
   uint64_t* buckets = nullptr;
   uint32_t* masks = nullptr;
-  uint32_t* locks = nullptr;
+  uint32_t* locks = nullptr;  // [2 nb_max]: bucket locks, then bucket versions
   uint64_t* stash_kv = nullptr;
   uint32_t* stash_keys = nullptr;
   hive::Ctrl* ctrl = nullptr;

@@ -24,22 +24,31 @@
 #include <stdint.h>
 
 #include "hive_internal.h"
+#include "hive_device.cuh"
 
 namespace hive {
 namespace {
 
-constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kOpsThreads = 256;
 #ifndef HIVE_MULTI_MIN_BLOCKS
 #define HIVE_MULTI_MIN_BLOCKS 3  // the multi-table bulk kernel also holds a table view per warp
 #endif
-#ifndef HIVE_STAGED_MODES
 // Bulk-kernel modes (bit kModeFind, kModeInsert, ...) whose probes are staged
-// in shared memory by bulk copies; the others load fragments straight from
-// global memory.  Staging pays for insert batches, whose paired probe reads
-// both buckets of every op; finds and mixed batches run faster with four
-// direct-load blocks per SM than with three staged ones.
-#define HIVE_STAGED_MODES 0x2
+// in shared memory by bulk copies, per bucket width; the others load
+// fragments straight from global memory with the warp-wide match-and-elect.
+// Measured on the 2^26-slot, 95%-load bench workload: staging wins for
+// insert, erase and mixed batches at both widths, and for finds at S = 32
+// (18.2 against 16.4 Gops/s); S = 16 finds stay direct (29.0 against 23.4).
+#ifndef HIVE_STAGED_MODES_S16
+#define HIVE_STAGED_MODES_S16 0xE
+#endif
+#ifndef HIVE_STAGED_MODES_S32
+#define HIVE_STAGED_MODES_S32 0xF
+#endif
+#ifndef HIVE_PAIRED_ANY
+// Staged erase and mixed batches copy both candidate buckets of every op in
+// one round instead of one bucket per round.
+#define HIVE_PAIRED_ANY 0
 #endif
 #ifndef HIVE_STAGED_MIN_BLOCKS
 #define HIVE_STAGED_MIN_BLOCKS 3  // 64 KB of staging per block: three blocks fit an SM
@@ -48,53 +57,15 @@ constexpr int kOpsThreads = 256;
 #define HIVE_OPS_MIN_BLOCKS 4  // resident 256-thread blocks per SM the bulk kernel is built for
 #endif
 constexpr int kOvfThreads = 256;
+__host__ __device__ constexpr bool staged_mode(int mode, int S) {
+  return ((S == 16 ? HIVE_STAGED_MODES_S16 : HIVE_STAGED_MODES_S32) >> mode) & 1;
+}
 constexpr int kMaintThreads = 1024;
 constexpr unsigned kMaintSmemWords = 8192;  // 64 KB of words sorted in shared memory
-
-// Per-op status codes (same numbers as include/hive.h).
-enum : uint8_t {
-  ST_INSERTED = 0,
-  ST_REPLACED = 1,
-  ST_ERASED = 2,
-  ST_NOT_FOUND = 3,
-  ST_FOUND = 4,
-  ST_FULL = 5,
-  ST_RESERVED = 6
-};
-enum : uint32_t { OP_INSERT = 0, OP_FIND = 1, OP_ERASE = 2 };
 
 // ----------------------------------------------------------------------------
 // Hashing and addressing
 // ----------------------------------------------------------------------------
-
-// BitHash1 (Section III-C, Listing 1) without the final reduction: a
-// Wang-style shift/xor/multiply avalanche.
-__device__ __forceinline__ uint32_t bithash1(uint32_t k) {
-  uint32_t x = (k << 15) - k - 1u;
-  x = x ^ (x >> 12);
-  x = x + (x << 2);
-  x = x ^ (x >> 4);
-  x = x * 2057u;
-  return x ^ (x >> 16);
-}
-
-// BitHash2 (Section III-C, Listing 1) without the final reduction: Jenkins'
-// six-step add/xor/shift mix.
-__device__ __forceinline__ uint32_t bithash2(uint32_t k) {
-  uint32_t x = k * 4097u + 0x7ED55D16u;
-  x = x ^ (x >> 19) ^ 0xC761C23Cu;
-  x = x * 33u + 0x165667B1u;
-  x = (x + 0xD3A2646Cu) ^ (x << 9);
-  x = x * 9u + 0xFD7046C5u;
-  return x ^ (x >> 16) ^ 0xB55A4F09u;
-}
-
-// Linear-hashing address (Section IV-C): buckets below the split pointer have
-// been split this round and use one more hash bit.
-__device__ __forceinline__ uint32_t lh_bucket(uint32_t h, uint32_t M, uint32_t p) {
-  const uint32_t b = h & M;
-  return b < p ? (h & (2u * M + 1u)) : b;
-}
 
 __device__ __forceinline__ uint64_t pack(uint32_t k, uint32_t v) {
   return (static_cast<uint64_t>(v) << 32) | k;
@@ -117,65 +88,6 @@ __device__ __forceinline__ void ld_frag(const uint64_t* p, uint64_t& a, uint64_t
                : "=l"(a), "=l"(b)
                : "l"(p)
                : "memory");
-}
-__device__ __forceinline__ uint64_t ld_relaxed64(const uint64_t* p) {
-  uint64_t r;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(r) : "l"(p) : "memory");
-  return r;
-}
-__device__ __forceinline__ uint32_t ld_relaxed32(const uint32_t* p) {
-  uint32_t r;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");
-  return r;
-}
-__device__ __forceinline__ void st_relaxed64(uint64_t* p, uint64_t v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long* ull(uint64_t* p) {
-  return reinterpret_cast<unsigned long long*>(p);
-}
-
-// ---- TMA bulk copies (cp.async.bulk) into shared memory, mbarrier-tracked ----
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// One bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
-// from global to shared memory, completing on `bar`.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-// Orders this thread's earlier generic-proxy shared-memory accesses before
-// later async-proxy (bulk copy) writes to the same memory.
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void lds_frag(const uint64_t* p, uint64_t& a, uint64_t& b) {
-  asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(smem_u32(p)));
 }
 
 // ----------------------------------------------------------------------------
@@ -366,19 +278,22 @@ __device__ __forceinline__ bool stage_round(const View& v, Stage& sg, unsigned n
 // (held by lane j, its home lane) must read bucket `myb` this round.  Load u
 // (u = 0..3) of lane group q (L lanes) reads the bucket of op Q*u + q of the
 // current group of 4Q ops, 16 bytes (two slots) per lane, so each load
-// instruction probes Q buckets -- from global memory, or with STAGED from the
-// warp's shared-memory copy `sbuf` of the round's buckets (buffer bucket j =
-// op j).  Match-and-elect (Section III-F) is a ballot per load: the lowest
+// instruction probes Q buckets.  Match-and-elect (Section III-F) is a ballot per load: the lowest
 // matching lane of a group is the winner, and one shuffle per load hands the
 // matched value to every home lane, which then reads its own op's outcome out
 // of the warp-uniform ballots.  A home lane that must update the matched slot
 // (erase, replace) does the single CAS itself: the expected word is
 // (value << 32 | key), both of which it now holds.
-template <int MODE, int S, bool STAGED>
+//
+// FUSED (the single-kernel batch): a word may be swapped out of its bucket by
+// a concurrent eviction chain, so a failed update CAS sets `retry` (the op
+// probes again) instead of flagging a contract violation, and an op counts as
+// done only once its CAS has succeeded.
+template <int MODE, int S, bool FUSED = false>
 __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb, uint32_t key,
                                       uint32_t val, uint32_t op, int lane, bool& done,
                                       uint8_t& st, uint32_t& outv, uint32_t& fcnt,
-                                      uint32_t& fslot, LaneCounters& cnt, const uint64_t* sbuf) {
+                                      uint32_t& fslot, LaneCounters& cnt, bool& retry) {
   constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
   constexpr int L = Geo<S>::L, Q = Geo<S>::Q;
   constexpr unsigned LM = Geo<S>::LM;
@@ -397,27 +312,17 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int src = G * g + Q * u + q;
-      if (STAGED) {
-        kq[u] = __shfl_sync(kFull, key, src);
-        if ((gneed >> (Q * u + q)) & 1u) {
-          lds_frag(sbuf + src * S + 2 * ql, wa[u], wb[u]);
-        } else {
-          wa[u] = kEmptyWord;
-          wb[u] = kEmptyWord;
-        }
+      const uint32_t bq = __shfl_sync(kFull, myb, src);
+      kq[u] = __shfl_sync(kFull, key, src);
+      if ((gneed >> (Q * u + q)) & 1u) {
+        const uint64_t* p = v.buckets + static_cast<uint64_t>(bq) * S + 2 * ql;
+        if (MODE == kModeFind)
+          ld_frag_ro(p, wa[u], wb[u]);
+        else
+          ld_frag(p, wa[u], wb[u]);
       } else {
-        const uint32_t bq = __shfl_sync(kFull, myb, src);
-        kq[u] = __shfl_sync(kFull, key, src);
-        if ((gneed >> (Q * u + q)) & 1u) {
-          const uint64_t* p = v.buckets + static_cast<uint64_t>(bq) * S + 2 * ql;
-          if (MODE == kModeFind)
-            ld_frag_ro(p, wa[u], wb[u]);
-          else
-            ld_frag(p, wa[u], wb[u]);
-        } else {
-          wa[u] = kEmptyWord;
-          wb[u] = kEmptyWord;
-        }
+        wa[u] = kEmptyWord;
+        wb[u] = kEmptyWord;
       }
     }
     unsigned my_m = 0, my_mh = 0, my_el = 0, my_eh = 0;
@@ -444,7 +349,7 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
     if (my_g == g && ((gneed >> my_j) & 1u)) {
       const unsigned hm = (my_m >> (L * my_q)) & LM;
       if (hm) {
-        done = true;
+        if (!FUSED) done = true;
         const uint32_t opk = MODE == kModeMixed
                                  ? op
                                  : (MODE == kModeFind ? OP_FIND
@@ -452,6 +357,7 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
         if (opk == OP_FIND) {
           outv = got;
           st = ST_FOUND;
+          done = true;
         } else {
           const uint32_t w = __ffs(hm) - 1;
           const uint32_t slot = 2 * w + ((my_mh >> (L * my_q + w)) & 1u);
@@ -461,20 +367,29 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
             // Algorithm 4: CAS the slot to EMPTY, then publish the free bit.
             // The atomicOr issues only after the CAS has returned, so a
             // claimer that sees the bit finds the slot already EMPTY.
-            st = ST_ERASED;
             if (atomicCAS(ull(sp), cur, kEmptyWord) == cur) {
               atomicOr(v.masks + myb, 1u << slot);
               cnt.size_delta -= 1;
+              st = ST_ERASED;
+              done = true;
+            } else if (FUSED) {
+              retry = true;
             } else {
+              st = ST_ERASED;
               cnt.contract = true;
             }
           } else {
             // Algorithm 1: CAS the cached word to the new pair.
-            st = ST_REPLACED;
-            if (atomicCAS(ull(sp), cur, pack(key, val)) == cur)
+            if (atomicCAS(ull(sp), cur, pack(key, val)) == cur) {
               cnt.replaced += 1;
-            else
+              st = ST_REPLACED;
+              done = true;
+            } else if (FUSED) {
+              retry = true;
+            } else {
+              st = ST_REPLACED;
               cnt.contract = true;
+            }
           }
         }
       } else if (kIns) {
@@ -494,17 +409,15 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
 // P = Q / 2 ops per load instruction.  An insert of a new key needs both
 // buckets anyway (step 1 must rule the key out of both before step 2 claims),
 // so this halves the dependent probe rounds of the find-shaped probe() above.
-// Covers the op groups of ops [o0, o1); with STAGED the fragments come from
-// `sbuf`, which holds op j's buckets at buffer buckets 2 (j - o0) and
-// 2 (j - o0) + 1.  On a match the home lane replaces the value with one CAS
+// Covers the op groups of ops [o0, o1).  On a match the home lane replaces the value with one CAS
 // (Algorithm 1); otherwise it records each bucket's free count and first
 // free slot.
-template <int S, bool STAGED>
+template <int S>
 __device__ __forceinline__ void probe_pair(const View& v, unsigned need, uint32_t b1,
                                            uint32_t b2, uint32_t key, uint32_t val, int lane,
                                            bool& done, uint8_t& st, uint32_t& f1, uint32_t& s1,
-                                           uint32_t& f2, uint32_t& s2, LaneCounters& cnt,
-                                           const uint64_t* sbuf, int o0, int o1) {
+                                           uint32_t& f2, uint32_t& s2, LaneCounters& cnt, int o0,
+                                           int o1) {
   constexpr int L = Geo<S>::L, Q = Geo<S>::Q;
   constexpr unsigned LM = Geo<S>::LM;
   constexpr int P = Q / 2;    // ops per load instruction
@@ -523,25 +436,15 @@ __device__ __forceinline__ void probe_pair(const View& v, unsigned need, uint32_
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int src = G * g + P * u + (q >> 1);
-      if (STAGED) {
-        kq[u] = __shfl_sync(kFull, key, src);
-        if ((gneed >> (P * u + (q >> 1))) & 1u) {
-          lds_frag(sbuf + (2 * (src - o0) + (q & 1)) * S + 2 * ql, wa[u], wb[u]);
-        } else {
-          wa[u] = kEmptyWord;
-          wb[u] = kEmptyWord;
-        }
+      const uint32_t q1 = __shfl_sync(kFull, b1, src);
+      const uint32_t q2 = __shfl_sync(kFull, b2, src);
+      kq[u] = __shfl_sync(kFull, key, src);
+      if ((gneed >> (P * u + (q >> 1))) & 1u) {
+        const uint64_t* p = v.buckets + static_cast<uint64_t>((q & 1) ? q2 : q1) * S + 2 * ql;
+        ld_frag(p, wa[u], wb[u]);
       } else {
-        const uint32_t q1 = __shfl_sync(kFull, b1, src);
-        const uint32_t q2 = __shfl_sync(kFull, b2, src);
-        kq[u] = __shfl_sync(kFull, key, src);
-        if ((gneed >> (P * u + (q >> 1))) & 1u) {
-          const uint64_t* p = v.buckets + static_cast<uint64_t>((q & 1) ? q2 : q1) * S + 2 * ql;
-          ld_frag(p, wa[u], wb[u]);
-        } else {
-          wa[u] = kEmptyWord;
-          wb[u] = kEmptyWord;
-        }
+        wa[u] = kEmptyWord;
+        wb[u] = kEmptyWord;
       }
     }
     unsigned my_m = 0, my_mh = 0, my_el = 0, my_eh = 0;
@@ -597,6 +500,63 @@ __device__ __forceinline__ void probe_pair(const View& v, unsigned need, uint32_
   }
 }
 
+// A single-bucket probe round on staged buckets, one op per lane: lane j
+// scans buffer bucket j (its op's bucket this round) with swizzled 16-byte
+// reads, as scan_staged_pair() below does for both buckets, and acts on a
+// match exactly as probe() does.  `mask` is the bucket's free mask, read while
+// the copies were in flight (insert-capable modes), for the claim.
+template <int MODE, int S>
+__device__ __forceinline__ void scan_staged_one(const View& v, const uint64_t* sbuf, int lane,
+                                                uint32_t myb, uint32_t key, uint32_t val,
+                                                uint32_t op, uint32_t mask, bool& done,
+                                                uint8_t& st, uint32_t& outv, uint32_t& fcnt,
+                                                uint32_t& fslot, LaneCounters& cnt) {
+  constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
+  constexpr int NP = S / 2;
+  const uint64_t* B = sbuf + lane * S;
+  int ms = -1;
+#pragma unroll 8
+  for (int k = 0; k < NP; ++k) {
+    const int f = (k + lane) & (NP - 1);
+    uint64_t a, b;
+    lds_frag(B + 2 * f, a, b);
+    if (key_of(a) == key) ms = 2 * f;
+    if (key_of(b) == key) ms = 2 * f + 1;
+  }
+  if (ms >= 0) {
+    done = true;
+    const uint64_t cur = B[ms];
+    const uint32_t opk = MODE == kModeMixed
+                             ? op
+                             : (MODE == kModeFind ? OP_FIND
+                                                  : (MODE == kModeErase ? OP_ERASE : OP_INSERT));
+    if (opk == OP_FIND) {
+      outv = val_of(cur);
+      st = ST_FOUND;
+    } else {
+      uint64_t* sp = v.buckets + static_cast<uint64_t>(myb) * S + ms;
+      if (opk == OP_ERASE) {
+        st = ST_ERASED;
+        if (atomicCAS(ull(sp), cur, kEmptyWord) == cur) {
+          atomicOr(v.masks + myb, 1u << ms);
+          cnt.size_delta -= 1;
+        } else {
+          cnt.contract = true;
+        }
+      } else {
+        st = ST_REPLACED;
+        if (atomicCAS(ull(sp), cur, pack(key, val)) == cur)
+          cnt.replaced += 1;
+        else
+          cnt.contract = true;
+      }
+    }
+  } else if (kIns) {
+    fcnt = __popc(mask);
+    fslot = mask ? __ffs(mask) - 1 : S;
+  }
+}
+
 // A single-bucket probe round, staged when the warp has a live stage.
 template <int MODE, int S>
 __device__ __forceinline__ void probe_round(const View& v, unsigned need, uint32_t myb,
@@ -604,12 +564,177 @@ __device__ __forceinline__ void probe_round(const View& v, unsigned need, uint32
                                             bool& done, uint8_t& st, uint32_t& outv,
                                             uint32_t& fcnt, uint32_t& fslot, LaneCounters& cnt,
                                             Stage* sg) {
-  if (sg && !sg->dead && stage_round<S, false>(v, *sg, need, 0, myb, 0, lane))
-    probe<MODE, S, true>(v, need, myb, key, val, op, lane, done, st, outv, fcnt, fslot, cnt,
-                         sg->buf);
-  else
-    probe<MODE, S, false>(v, need, myb, key, val, op, lane, done, st, outv, fcnt, fslot, cnt,
-                          nullptr);
+  constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
+  if (sg && !sg->dead) {
+    const bool mine = (need >> lane) & 1u;
+    const uint32_t m = (kIns && mine) ? ld_relaxed32(v.masks + myb) : 0u;
+    if (stage_round<S, false>(v, *sg, need, 0, myb, 0, lane)) {
+      if (mine)
+        scan_staged_one<MODE, S>(v, sg->buf, lane, myb, key, val, op, m, done, st, outv, fcnt,
+                                 fslot, cnt);
+      return;
+    }
+  }
+  bool unused = false;
+  probe<MODE, S>(v, need, myb, key, val, op, lane, done, st, outv, fcnt, fslot, cnt, unused);
+}
+
+// Erase and mixed batches, staged: both candidate buckets of every op are
+// copied in one round (a probe round trip instead of two), and each lane
+// scans its op's two buckets in BitHash1-then-BitHash2 order and acts on the
+// first match exactly as probe() does.  Reading the BitHash2 bucket of an op
+// that hits in its BitHash1 bucket is speculative: it costs bytes, which these
+// latency-bound batches have to spare, and is not counted as a probe.
+// Returns the probes the op needed (1 on a BitHash1 hit, else 2).
+template <int MODE, int S>
+__device__ __forceinline__ uint32_t scan_staged_any(const View& v, const uint64_t* sbuf, int jj,
+                                                    uint32_t b1, uint32_t b2, uint32_t key,
+                                                    uint32_t val, uint32_t op, uint32_t m1,
+                                                    uint32_t m2, bool& done, uint8_t& st,
+                                                    uint32_t& outv, uint32_t& f1, uint32_t& s1,
+                                                    uint32_t& f2, uint32_t& s2,
+                                                    LaneCounters& cnt) {
+  constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
+  constexpr int NP = S / 2;
+  const uint64_t* B = sbuf + 2 * jj * S;
+  int ms = -1;
+#pragma unroll
+  for (int which = 0; which < 2; ++which) {
+    if (ms >= 0) break;
+#pragma unroll 8
+    for (int k = 0; k < NP; ++k) {
+      const int f = (k + jj) & (NP - 1);
+      uint64_t a, b;
+      lds_frag(B + which * S + 2 * f, a, b);
+      if (key_of(a) == key) ms = which * S + 2 * f;
+      if (key_of(b) == key) ms = which * S + 2 * f + 1;
+    }
+  }
+  if (ms >= 0) {
+    done = true;
+    const uint64_t cur = B[ms];
+    const uint32_t b = ms < S ? b1 : b2;
+    const uint32_t slot = ms & (S - 1);
+    const uint32_t opk = MODE == kModeMixed ? op : (MODE == kModeErase ? OP_ERASE : OP_FIND);
+    if (opk == OP_FIND) {
+      outv = val_of(cur);
+      st = ST_FOUND;
+    } else {
+      uint64_t* sp = v.buckets + static_cast<uint64_t>(b) * S + slot;
+      if (opk == OP_ERASE) {
+        st = ST_ERASED;
+        if (atomicCAS(ull(sp), cur, kEmptyWord) == cur) {
+          atomicOr(v.masks + b, 1u << slot);
+          cnt.size_delta -= 1;
+        } else {
+          cnt.contract = true;
+        }
+      } else {
+        st = ST_REPLACED;
+        if (atomicCAS(ull(sp), cur, pack(key, val)) == cur)
+          cnt.replaced += 1;
+        else
+          cnt.contract = true;
+      }
+    }
+    return ms < S ? 1u : 2u;
+  }
+  if (kIns) {
+    f1 = __popc(m1);
+    f2 = __popc(m2);
+    s1 = m1 ? __ffs(m1) - 1 : S;
+    s2 = m2 ? __ffs(m2) - 1 : S;
+  }
+  return 2u;
+}
+
+// The paired staged round of erase and mixed batches, in batches of 512 / S
+// ops.  A stage that has given up falls back to the two direct rounds.
+template <int MODE, int S>
+__device__ __forceinline__ void probe_any_paired(const View& v, unsigned need, uint32_t b1,
+                                                 uint32_t b2, uint32_t key, uint32_t val,
+                                                 uint32_t op, int lane, bool& done, uint8_t& st,
+                                                 uint32_t& outv, uint32_t& f1, uint32_t& s1,
+                                                 uint32_t& f2, uint32_t& s2, LaneCounters& cnt,
+                                                 Stage* sg) {
+  constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
+  constexpr int BO = kStageWords / (2 * S);
+  constexpr unsigned BM = (BO >= 32) ? 0xFFFFFFFFu : ((1u << BO) - 1u);
+  const bool mine = (need >> lane) & 1u;
+  const bool ins = kIns && mine && op == OP_INSERT;
+  const uint32_t m1 = ins ? ld_relaxed32(v.masks + b1) : 0u;
+  const uint32_t m2 = ins ? ld_relaxed32(v.masks + b2) : 0u;
+  uint32_t probes = 0;
+  unsigned rest = need;
+#pragma unroll 1
+  for (int o0 = 0; o0 < 32 && !sg->dead; o0 += BO) {
+    const unsigned bneed = need & (BM << o0);
+    if (!bneed) continue;
+    if (!stage_round<S, true>(v, *sg, bneed, o0, b1, b2, lane)) break;
+    rest &= ~bneed;
+    if ((bneed >> lane) & 1u)
+      probes = scan_staged_any<MODE, S>(v, sg->buf, lane - o0, b1, b2, key, val, op, m1, m2, done,
+                                        st, outv, f1, s1, f2, s2, cnt);
+  }
+  cnt.probes += __reduce_add_sync(kFull, probes);
+  if (rest) {  // a staged wait gave up: the rest of the ops probe directly
+    bool unused = false;
+    cnt.probes += __popc(rest);
+    probe<MODE, S>(v, rest, b1, key, val, op, lane, done, st, outv, f1, s1, cnt, unused);
+    rest = __ballot_sync(kFull, ((rest >> lane) & 1u) && !done);
+    cnt.probes += __popc(rest);
+    if (rest) probe<MODE, S>(v, rest, b2, key, val, op, lane, done, st, outv, f2, s2, cnt, unused);
+  }
+}
+
+// The paired insert round on staged buckets, one op per lane.  With both
+// candidate buckets of its op in shared memory, a lane scans them itself:
+// S / 2 16-byte fragment reads per bucket, starting at fragment (op mod S / 2)
+// so that the eight lanes of a shared-memory wavefront read eight different
+// bank groups, and one compare per slot against the op's key (a key sits in
+// at most one slot of the table).  Free counts and first free slots come from
+// the free masks, read from global memory while the bulk copies are in flight:
+// they only steer the claim, whose fetch_and result is the authority.  This
+// takes a few instructions per slot where the warp-wide match-and-elect takes
+// several ballots per 16-byte fragment, and the staged kernel is bound by
+// instruction issue, not by memory.
+template <int S>
+__device__ __forceinline__ void scan_staged_pair(const View& v, const uint64_t* sbuf, int jj,
+                                                 uint32_t b1, uint32_t b2, uint32_t key,
+                                                 uint32_t val, uint32_t m1, uint32_t m2,
+                                                 bool& done, uint8_t& st, uint32_t& f1,
+                                                 uint32_t& s1, uint32_t& f2, uint32_t& s2,
+                                                 LaneCounters& cnt) {
+  constexpr int NP = S / 2;  // 16-byte fragments per bucket
+  const uint64_t* B = sbuf + 2 * jj * S;
+  int ms = -1;  // matched word in [0, 2S): bucket ms / S, slot ms % S
+#pragma unroll
+  for (int which = 0; which < 2; ++which) {
+#pragma unroll 8
+    for (int k = 0; k < NP; ++k) {
+      const int f = (k + jj) & (NP - 1);
+      uint64_t a, b;
+      lds_frag(B + which * S + 2 * f, a, b);
+      if (key_of(a) == key) ms = which * S + 2 * f;
+      if (key_of(b) == key) ms = which * S + 2 * f + 1;
+    }
+  }
+  if (ms >= 0) {
+    done = true;
+    st = ST_REPLACED;
+    const uint64_t cur = B[ms];
+    const uint32_t b = ms < S ? b1 : b2;
+    uint64_t* sp = v.buckets + static_cast<uint64_t>(b) * S + (ms & (S - 1));
+    if (atomicCAS(ull(sp), cur, pack(key, val)) == cur)
+      cnt.replaced += 1;
+    else
+      cnt.contract = true;
+  } else {
+    f1 = __popc(m1);
+    f2 = __popc(m2);
+    s1 = m1 ? __ffs(m1) - 1 : S;
+    s2 = m2 ? __ffs(m2) - 1 : S;
+  }
 }
 
 // The paired insert round, staged in batches of 512 / S ops when the warp has
@@ -623,21 +748,25 @@ __device__ __forceinline__ void probe_pair_round(const View& v, unsigned need, u
   constexpr int BO = kStageWords / (2 * S);
   constexpr unsigned BM = (BO >= 32) ? 0xFFFFFFFFu : ((1u << BO) - 1u);
   if (sg) {
+    // free masks of both buckets, in flight beside the bulk copies
+    const bool mine = (need >> lane) & 1u;
+    const uint32_t m1 = mine ? ld_relaxed32(v.masks + b1) : 0u;
+    const uint32_t m2 = mine ? ld_relaxed32(v.masks + b2) : 0u;
 #pragma unroll 1
     for (int o0 = 0; o0 < 32; o0 += BO) {
       const unsigned bneed = need & (BM << o0);
       if (!bneed) continue;
       if (sg->dead || !stage_round<S, true>(v, *sg, bneed, o0, b1, b2, lane)) {
-        probe_pair<S, false>(v, need & ~((1u << o0) - 1u), b1, b2, key, val, lane, done, st, f1,
-                             s1, f2, s2, cnt, nullptr, o0, 32);
+        probe_pair<S>(v, need & ~((1u << o0) - 1u), b1, b2, key, val, lane, done, st, f1, s1, f2,
+                      s2, cnt, o0, 32);
         return;
       }
-      probe_pair<S, true>(v, bneed, b1, b2, key, val, lane, done, st, f1, s1, f2, s2, cnt,
-                          sg->buf, o0, o0 + BO);
+      if ((bneed >> lane) & 1u)
+        scan_staged_pair<S>(v, sg->buf, lane - o0, b1, b2, key, val, m1, m2, done, st, f1, s1,
+                            f2, s2, cnt);
     }
   } else {
-    probe_pair<S, false>(v, need, b1, b2, key, val, lane, done, st, f1, s1, f2, s2, cnt, nullptr,
-                         0, 32);
+    probe_pair<S>(v, need, b1, b2, key, val, lane, done, st, f1, s1, f2, s2, cnt, 0, 32);
   }
 }
 
@@ -675,26 +804,43 @@ __device__ __forceinline__ void flush_counters(const View& v, LaneCounters& cnt,
   cnt = LaneCounters();
 }
 
-// Ops [32c, 32c + 32) of a batch of n ops on the table of `v`.  Full-bucket
-// inserts go to the overflow list, tagged with `seg` when the list keeps tags.
-template <int MODE, int S>
-__device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const OpPtrs a,
-                                          uint32_t c, uint64_t n, const List ovf, uint32_t seg,
-                                          LaneCounters& cnt, int lane, Stage* sg = nullptr) {
+// One op's inputs (op code, key, value).
+struct OpIn {
+  uint32_t op, key, val;
+};
+
+template <int MODE>
+__device__ __forceinline__ OpIn load_in(const OpPtrs& a, uint32_t c, uint64_t n, int lane) {
   constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
   const uint32_t i = (c << 5) + lane;
   const bool valid = i < n;
-  uint32_t op = OP_FIND;
+  OpIn in;
+  in.op = OP_FIND;
   if (MODE == kModeMixed)
-    op = valid ? static_cast<uint32_t>(__ldcs(a.ops + i)) : OP_FIND;
+    in.op = valid ? static_cast<uint32_t>(__ldcs(a.ops + i)) : OP_FIND;
   else if (MODE == kModeInsert)
-    op = OP_INSERT;
+    in.op = OP_INSERT;
   else if (MODE == kModeErase)
-    op = OP_ERASE;
-  if (op > OP_ERASE) op = OP_FIND;  // unknown op codes read only
-  const uint32_t key = valid ? __ldcs(a.keys + i) : kEmptyKey;
-  uint32_t val = 0;
-  if (kIns && valid && op == OP_INSERT && a.vals) val = __ldcs(a.vals + i);
+    in.op = OP_ERASE;
+  if (in.op > OP_ERASE) in.op = OP_FIND;  // unknown op codes read only
+  in.key = valid ? __ldcs(a.keys + i) : kEmptyKey;
+  in.val = (kIns && valid && in.op == OP_INSERT && a.vals) ? __ldcs(a.vals + i) : 0u;
+  return in;
+}
+
+// Ops [32c, 32c + 32) of a batch of n ops on the table of `v`.  Full-bucket
+// inserts go to the overflow list, tagged with `seg` when the list keeps tags.
+// `pre` holds the chunk's inputs when the caller loaded them ahead.
+template <int MODE, int S>
+__device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const OpPtrs a,
+                                          uint32_t c, uint64_t n, const List ovf, uint32_t seg,
+                                          LaneCounters& cnt, int lane, Stage* sg = nullptr,
+                                          const OpIn* pre = nullptr) {
+  constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
+  const uint32_t i = (c << 5) + lane;
+  const bool valid = i < n;
+  const OpIn in = pre ? *pre : load_in<MODE>(a, c, n, lane);
+  const uint32_t op = in.op, key = in.key, val = in.val;
   const bool reserved = valid && key >= kReservedKeyMin;
   const bool live = valid && !reserved;
   cnt.reserved |= reserved;
@@ -712,6 +858,10 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
   if (MODE == kModeInsert) {
     cnt.probes += 2 * __popc(need);
     if (need) probe_pair_round<S>(v, need, b1, b2, key, val, lane, done, st, f1, s1, f2, s2, cnt, sg);
+  } else if ((MODE == kModeErase || MODE == kModeMixed) && HIVE_PAIRED_ANY && sg) {
+    if (need)
+      probe_any_paired<MODE, S>(v, need, b1, b2, key, val, op, lane, done, st, outv, f1, s1, f2,
+                                s2, cnt, sg);
   } else {
     cnt.probes += __popc(need);
     if (need) probe_round<MODE, S>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt, sg);
@@ -800,7 +950,7 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
 }
 
 template <int MODE, int S>
-__global__ void __launch_bounds__(kOpsThreads, ((HIVE_STAGED_MODES >> MODE) & 1)
+__global__ void __launch_bounds__(kOpsThreads, staged_mode(MODE, S)
                                                    ? HIVE_STAGED_MIN_BLOCKS
                                                    : HIVE_OPS_MIN_BLOCKS)
     k_ops(View v, OpPtrs a, uint64_t n, List ovf) {
@@ -811,12 +961,19 @@ __global__ void __launch_bounds__(kOpsThreads, ((HIVE_STAGED_MODES >> MODE) & 1)
   const uint32_t nchunks = static_cast<uint32_t>((n + 31) >> 5);
   const uint32_t stash_n = v.ctrl->stash_n;
   LaneCounters cnt;
-  if ((HIVE_STAGED_MODES >> MODE) & 1) {
+  if (staged_mode(MODE, S)) {
     // bucket reads staged in shared memory by bulk copies
     extern __shared__ __align__(16) uint64_t ops_smem[];
     Stage sg = stage_init(ops_smem, threadIdx.x >> 5, lane);
-    for (uint32_t c = warp0; c < nchunks; c += nwarps)
-      run_chunk<MODE, S>(v, stash_n, a, c, n, ovf, 0, cnt, lane, &sg);
+    // inputs are loaded one chunk ahead, so their latency hides behind the
+    // current chunk's probes and claims
+    OpIn nxt{};
+    if (warp0 < nchunks) nxt = load_in<MODE>(a, warp0, n, lane);
+    for (uint32_t c = warp0; c < nchunks; c += nwarps) {
+      const OpIn cur = nxt;
+      if (c + nwarps < nchunks) nxt = load_in<MODE>(a, c + nwarps, n, lane);
+      run_chunk<MODE, S>(v, stash_n, a, c, n, ovf, 0, cnt, lane, &sg, &cur);
+    }
     stage_drain(sg);
   } else {
     for (uint32_t c = warp0; c < nchunks; c += nwarps)
@@ -1023,6 +1180,361 @@ __global__ void __launch_bounds__(kOvfThreads)
     overflow_item<S>(v, in.words[it], in.idx[it], 0, status, resizable, pend, oc, lane);
   release_reservation(oc, lane);
   flush_ovf_counters(v, oc, lane);
+}
+
+// ----------------------------------------------------------------------------
+// Concurrent mixed batch in one kernel (the paper's single-kernel mode)
+// ----------------------------------------------------------------------------
+//
+// Here finds, erases, replaces, claims and eviction chains of one batch run
+// at the same time, so a lookup can race with a chain that has taken a word
+// out of a bucket and not yet put it down.  Each bucket has a version word:
+// bits 16..31 count the chains holding a word that was taken out of this
+// bucket (in transit), bits 0..15 count chain steps that finished.  A chain
+// raises the transit count of a bucket before it swaps a word out of it and
+// lowers it (bumping the step count) once that word sits in its other bucket
+// or in the stash, with a fence on each side.  A lookup reads the versions of
+// both candidate buckets before probing and again after a miss; the miss
+// stands only if neither bucket had a word in transit and neither version
+// moved, otherwise the op probes again.  A hit needs no check: the word was
+// observed in place.  Because erases now run beside chains, a chain swaps its
+// victim with a CAS on the word it read (never onto an EMPTY slot), and every
+// claim publishes with a CAS, exactly as in the eviction kernel.
+constexpr uint32_t kTransit = 1u << 16;
+constexpr uint32_t kFusedRetryLimit = 1u << 14;
+
+__device__ __forceinline__ void transit_begin(const View& v, uint32_t b) {
+  atomicAdd(v.vers + b, kTransit);
+  __threadfence();
+}
+__device__ __forceinline__ void transit_end(const View& v, uint32_t b) {
+  __threadfence();
+  atomicAdd(v.vers + b, 1u - kTransit);
+}
+
+// Steps 3-4 for one new key whose candidate buckets had no free slot, run by
+// the warp inside the single-kernel batch.  Returns 1 placed, 2 stashed,
+// 3 no room (pending or FULL, decided by the caller).
+template <int S>
+__device__ int fused_evict(const View& v, uint64_t word0, uint32_t b1, uint32_t b2,
+                           OvfCounters& oc, int lane) {
+  int outcome = 0;
+  if (lane == 0) {
+    const uint32_t m1 = ld_relaxed32(v.masks + b1);
+    const uint32_t m2 = ld_relaxed32(v.masks + b2);
+    if ((m1 && claim_cas<S>(v, b1, word0)) || (b2 != b1 && m2 && claim_cas<S>(v, b2, word0))) {
+      outcome = 1;
+      ++oc.claim;
+    } else {
+      if (oc.reserved_in != v.ctrl) {
+        if (oc.reserved_in) atomicSub(&oc.reserved_in->stash_claims, 1u);
+        oc.reserved_in = stash_reserve(v) ? v.ctrl : nullptr;
+      }
+      if (!oc.reserved_in) outcome = 3;
+    }
+  }
+  outcome = __shfl_sync(kFull, outcome, 0);
+  if (outcome != 0) return outcome;
+
+  uint64_t cur = word0;
+  uint32_t b = b1;
+  uint32_t held = kNoOp;  // bucket the word in hand was taken out of
+  bool placed = false;
+  for (uint32_t r = 0; r < v.max_evictions; ++r) {
+    const uint64_t w =
+        lane < S ? ld_relaxed64(v.buckets + static_cast<uint64_t>(b) * S + lane) : kEmptyWord;
+    uint32_t am = 0;
+    if (w != kEmptyWord) {
+      const uint32_t k = key_of(w);
+      const uint32_t a1 = lh_bucket(bithash1(k), v.M, v.p);
+      const uint32_t a2 = lh_bucket(bithash2(k), v.M, v.p);
+      const uint32_t alt = (a1 == b) ? a2 : a1;
+      if (alt != b) am = ld_relaxed32(v.masks + alt);
+    }
+    const unsigned gm = __ballot_sync(kFull, am != 0u);
+    const unsigned occ = __ballot_sync(kFull, lane < S && w != kEmptyWord);
+    const bool has_empty = __ballot_sync(kFull, lane < S && w == kEmptyWord) != 0u;
+    // victim: an occupied slot whose word can move on at once, else an
+    // occupied slot picked by rotation
+    uint32_t vs = S;
+    if (gm) {
+      vs = __ffs(gm) - 1;
+    } else if (occ) {
+      const uint32_t start = (bithash2(key_of(cur)) + r) & (S - 1);
+      const unsigned rot = (occ >> start) | (start ? (occ << (32 - start)) : 0u);
+      vs = (start + __ffs(rot) - 1) & 31;
+    }
+    const uint64_t wv = __shfl_sync(kFull, w, vs & 31);
+    const uint32_t vmask = __shfl_sync(kFull, am, vs & 31);
+    int res = 0;  // 0: swapped, 1: placed, 2: lock wait gave up, 3: redo the round
+    if (lane == 0) {
+      ++oc.rounds;
+      if (!lock_bucket(v, b)) {
+        res = 2;
+        ++oc.to;
+      } else {
+        ++oc.locks;
+        if (has_empty && claim_cas<S>(v, b, cur)) {
+          res = 1;
+        } else if (vs >= S) {
+          res = 3;
+        } else {
+          transit_begin(v, b);
+          uint64_t* sp = v.buckets + static_cast<uint64_t>(b) * S + vs;
+          if (atomicCAS(ull(sp), wv, cur) == wv) {
+            res = 0;
+          } else {
+            transit_end(v, b);
+            res = 3;
+          }
+        }
+        unlock_bucket(v, b);
+      }
+      // the word in hand now sits in b (placed or swapped in)
+      if ((res == 0 || res == 1) && held != kNoOp) transit_end(v, held);
+    }
+    res = __shfl_sync(kFull, res, 0);
+    if (res == 1) {
+      placed = true;
+      held = kNoOp;
+      break;
+    }
+    if (res == 2) break;
+    if (res == 3) continue;
+    held = b;
+    cur = wv;
+    const uint32_t kc = key_of(cur);
+    const uint32_t a1 = lh_bucket(bithash1(kc), v.M, v.p);
+    const uint32_t a2 = lh_bucket(bithash2(kc), v.M, v.p);
+    const uint32_t nb = (a1 == b) ? a2 : a1;
+    if (nb == b) break;
+    b = nb;
+    int ok = 0;
+    if (lane == 0) {
+      ok = claim_cas<S>(v, b, cur, vmask);
+      if (ok) transit_end(v, held);
+    }
+    if (__shfl_sync(kFull, ok, 0)) {
+      placed = true;
+      held = kNoOp;
+      break;
+    }
+  }
+  if (lane == 0) {
+    if (placed && oc.reserved_in && ld_relaxed32(&v.ctrl->stash_claims) >= v.stash_cap) {
+      atomicSub(&v.ctrl->stash_claims, 1u);
+      oc.reserved_in = nullptr;
+    }
+    if (!placed) {
+      oc.reserved_in = nullptr;
+      const unsigned pos = atomicAdd(&v.ctrl->stash_tail, 1u);
+      st_relaxed64(v.stash_kv + pos, cur);
+      ++oc.stash;
+      if (held != kNoOp) transit_end(v, held);
+    }
+  }
+  return placed ? 1 : 2;
+}
+
+// Looks the op keys of the `need` lanes up in the stash words appended during
+// this kernel, [from, to) (warp-wide).  A lane that finds its key gets its
+// position in `pos` and returns true.
+__device__ __forceinline__ bool stash_tail_find(const View& v, uint32_t from, uint32_t to,
+                                                unsigned need, uint32_t key, int lane,
+                                                uint32_t& pos) {
+  bool hit = false;
+  for (uint32_t base = from; base < to; base += 32) {
+    const uint32_t j = base + lane;
+    const uint64_t w = j < to ? ld_relaxed64(v.stash_kv + j) : kEmptyWord;
+    for (unsigned m = need; m; m &= m - 1) {
+      const int src = __ffs(m) - 1;
+      const uint32_t kj = __shfl_sync(kFull, key, src);
+      const unsigned eq = __ballot_sync(kFull, w != kEmptyWord && key_of(w) == kj);
+      if (lane == src && eq && !hit) {
+        hit = true;
+        pos = base + __ffs(eq) - 1;
+      }
+    }
+  }
+  return hit;
+}
+
+// Ops [32c, 32c + 32) of a mixed batch in the single-kernel mode.
+template <int S>
+__device__ __forceinline__ void run_chunk_fused(const View& v, uint32_t stash_n, const OpPtrs a,
+                                                uint32_t c, uint64_t n, const List pend,
+                                                int resizable, LaneCounters& cnt,
+                                                OvfCounters& oc, unsigned& retries, int lane) {
+  const uint32_t i = (c << 5) + lane;
+  const bool valid = i < n;
+  uint32_t op = valid ? static_cast<uint32_t>(__ldcs(a.ops + i)) : OP_FIND;
+  if (op > OP_ERASE) op = OP_FIND;
+  const uint32_t key = valid ? __ldcs(a.keys + i) : kEmptyKey;
+  uint32_t val = 0;
+  if (valid && op == OP_INSERT && a.vals) val = __ldcs(a.vals + i);
+  const bool reserved = valid && key >= kReservedKeyMin;
+  const bool live = valid && !reserved;
+  cnt.reserved |= reserved;
+  const uint32_t b1 = lh_bucket(bithash1(key), v.M, v.p);
+  const uint32_t b2 = lh_bucket(bithash2(key), v.M, v.p);
+  bool done = !live;
+  uint8_t st = reserved ? ST_RESERVED : ST_NOT_FOUND;
+  uint32_t outv = 0;
+  uint32_t f1 = 0, s1 = S, f2 = 0, s2 = S;
+  bool absent = false;  // a miss that survived the version check
+  for (uint32_t attempt = 0;; ++attempt) {
+    const bool active = !done && !absent;
+    unsigned need = __ballot_sync(kFull, active);
+    if (!need) break;
+    if (attempt >= kFusedRetryLimit) {  // never expected: chains end in bounded time
+      if (lane == 0) atomicOr(&v.ctrl->err, kErrTimeout);
+      break;
+    }
+    if (attempt) {
+      retries += (lane == 0) ? __popc(need) : 0u;
+      __nanosleep(64u << min(attempt, 6u));
+    }
+    uint32_t v1 = 0, v2 = 0;
+    if (active) {
+      v1 = ld_acquire32(v.vers + b1);
+      v2 = ld_acquire32(v.vers + b2);
+    }
+    bool retry = false;
+    cnt.probes += __popc(need);
+    probe<kModeMixed, S, true>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt,
+                               retry);
+    need = __ballot_sync(kFull, active && !done && !retry);
+    cnt.probes += __popc(need);
+    if (need)
+      probe<kModeMixed, S, true>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt,
+                                 retry);
+    // the stash: the sorted prefix, then what this kernel appended
+    bool miss = active && !done && !retry;
+    uint32_t pos = 0;
+    bool shit = false;
+    if (miss && stash_n) {
+      cnt.stash_lookups += 1;
+      shit = stash_find(v, stash_n, key, pos);
+    }
+    const uint32_t tail = ld_relaxed32(&v.ctrl->stash_tail);
+    const unsigned tneed = __ballot_sync(kFull, miss && !shit);
+    if (tneed && tail > stash_n) {
+      uint32_t tp = 0;
+      if (stash_tail_find(v, stash_n, min(tail, v.stash_cap), tneed, key, lane, tp) && miss && !shit) {
+        shit = true;
+        pos = tp;
+      }
+    }
+    if (shit) {
+      uint64_t* sp = v.stash_kv + pos;
+      const uint64_t w = ld_relaxed64(sp);
+      if (key_of(w) == key) {
+        if (op == OP_FIND) {
+          done = true;
+          outv = val_of(w);
+          st = ST_FOUND;
+        } else if (op == OP_ERASE) {
+          if (atomicCAS(ull(sp), w, kEmptyWord) == w) {
+            done = true;
+            st = ST_ERASED;
+            cnt.size_delta -= 1;
+            atomicExch(&v.ctrl->stash_dirty, 1u);
+          } else {
+            retry = true;
+          }
+        } else {
+          if (atomicCAS(ull(sp), w, pack(key, val)) == w) {
+            done = true;
+            st = ST_REPLACED;
+            cnt.replaced += 1;
+          } else {
+            retry = true;
+          }
+        }
+      }
+    }
+    if (active && !done && !retry) {
+      __threadfence();
+      const uint32_t w1 = ld_acquire32(v.vers + b1);
+      const uint32_t w2 = ld_acquire32(v.vers + b2);
+      absent = v1 < kTransit && v2 < kTransit && v1 == w1 && v2 == w2;
+    }
+  }
+
+  // New keys: claim in the preferred bucket (two-choice), else the other;
+  // keys that find both full run the eviction chain below.
+  bool to_evict = false;
+  if (absent && op == OP_INSERT) {
+    const uint64_t word = pack(key, val);
+    const bool first1 = v.placement ? (f1 > 0) : (f1 >= f2);
+    const uint32_t tb = first1 ? b1 : b2, ts = first1 ? s1 : s2;
+    const uint32_t ob = first1 ? b2 : b1, os = first1 ? s2 : s1;
+    bool placed = false;
+    if (f1 + f2 > 0) {
+      placed = claim_cas<S>(v, tb, word, ts < S ? (1u << ts) : 0u);
+      if (!placed && ob != tb) placed = claim_cas<S>(v, ob, word, os < S ? (1u << os) : 0u);
+    }
+    if (placed) {
+      st = ST_INSERTED;
+      cnt.size_delta += 1;
+      cnt.claimed += 1;
+    } else {
+      to_evict = true;
+      cnt.overflowed += 1;
+    }
+  }
+  for (unsigned m = __ballot_sync(kFull, to_evict); m; m &= m - 1) {
+    const int src = __ffs(m) - 1;
+    const uint64_t wj = __shfl_sync(kFull, pack(key, val), src);
+    const uint32_t x1 = __shfl_sync(kFull, b1, src);
+    const uint32_t x2 = __shfl_sync(kFull, b2, src);
+    const int out = fused_evict<S>(v, wj, x1, x2, oc, lane);
+    if (lane == 0) {  // the warp's eviction counters live in lane 0
+      if (out == 3)
+        ++oc.pend;
+      else
+        ++oc.added;
+    }
+    if (lane == src) {
+      if (out == 3) {
+        if (resizable) {
+          const unsigned p = atomicAdd(pend.count, 1u);
+          pend.words[p] = wj;
+          pend.idx[p] = i;
+          st = 0xFF;  // written by the pending pass
+        } else {
+          atomicOr(&v.ctrl->err, kErrFull);
+          st = ST_FULL;
+        }
+      } else {
+        st = ST_INSERTED;
+      }
+    }
+  }
+  if (valid) {
+    if (a.status && st != 0xFF) a.status[i] = st;
+    if (a.vals_out) __stcs(a.vals_out + i, outv);
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kOpsThreads, 3)
+    k_fused(View v, OpPtrs a, uint64_t n, List pend, int resizable) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t nchunks = static_cast<uint32_t>((n + 31) >> 5);
+  const uint32_t stash_n = v.ctrl->stash_n;
+  LaneCounters cnt;
+  OvfCounters oc;
+  unsigned retries = 0;
+  for (uint32_t c = warp0; c < nchunks; c += nwarps)
+    run_chunk_fused<S>(v, stash_n, a, c, n, pend, resizable, cnt, oc, retries, lane);
+  release_reservation(oc, lane);
+  flush_ovf_counters(v, oc, lane);
+  flush_counters(v, cnt, lane);
+  if (lane == 0 && retries)
+    atomicAdd(&v.ctrl->stats[kStFusedRetries], static_cast<unsigned long long>(retries));
 }
 
 // ----------------------------------------------------------------------------
@@ -1374,7 +1886,7 @@ cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys
   const uint64_t chunks = (n + 31) / 32;
   const uint64_t warps_per_block = kOpsThreads / 32;
   uint64_t blocks = (chunks + warps_per_block - 1) / warps_per_block;
-  constexpr bool kStaged = (HIVE_STAGED_MODES >> MODE) & 1;
+  constexpr bool kStaged = staged_mode(MODE, S);
   const int per_sm = kStaged ? L.staged_blocks_per_sm : L.ops_blocks_per_sm;
   const uint64_t cap = static_cast<uint64_t>(L.num_sms) * per_sm;
   if (blocks > cap) blocks = cap;
@@ -1402,6 +1914,23 @@ cudaError_t launch_ops_s(int mode, const View& v, const uint8_t* ops, const uint
 }
 
 }  // namespace
+
+cudaError_t launch_fused(const View& v, const uint8_t* ops, const uint32_t* keys,
+                         const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* status,
+                         List pend, int resizable, const Launch& L, cudaStream_t s) {
+  const uint64_t chunks = (n + 31) / 32;
+  const uint64_t warps_per_block = kOpsThreads / 32;
+  uint64_t blocks = (chunks + warps_per_block - 1) / warps_per_block;
+  const uint64_t cap = static_cast<uint64_t>(L.num_sms) * L.fused_blocks_per_sm;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  const OpPtrs a{ops, keys, vals, vals_out, nullptr, status};
+  if (v.S == 16)
+    k_fused<16><<<static_cast<unsigned>(blocks), kOpsThreads, 0, s>>>(v, a, n, pend, resizable);
+  else
+    k_fused<32><<<static_cast<unsigned>(blocks), kOpsThreads, 0, s>>>(v, a, n, pend, resizable);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ops(int mode, const View& v, const uint8_t* ops, const uint32_t* keys,
                        const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
@@ -1547,6 +2076,9 @@ cudaError_t occupancy_s(Launch* L) {
                                                     kStageSmemBytes);
   if (e != cudaSuccess) return e;
   L->staged_blocks_per_sm = b > 0 ? b : 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused<S>, kOpsThreads, 0);
+  if (e != cudaSuccess) return e;
+  L->fused_blocks_per_sm = b > 0 ? b : 1;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_multi_ops<S>, kOpsThreads, 0);
   if (e != cudaSuccess) return e;
   L->multi_blocks_per_sm = b > 0 ? b : 1;

@@ -28,12 +28,17 @@ PLACE_BALANCED, PLACE_FIRST = 0, 1
 MULTI_GRAPH, MULTI_ASYNC = 1, 2
 
 EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", "hive_find",
-           "hive_erase", "hive_execute", "hive_size", "hive_capacity", "hive_clear", "hive_check",
+           "hive_erase", "hive_execute", "hive_execute_fused", "hive_size", "hive_capacity", "hive_clear", "hive_check",
            "hive_stats", "hive_dump", "hive_profile_enable", "hive_profile_read",
            "hive_insert_noalloc", "hive_multi_create", "hive_multi_execute",
            "hive_multi_destroy", "hive_insert_host", "hive_find_host", "hive_execute_host",
-           "hive_reserve", "hive_memory", "hive_last_error"]
-KERNEL_KINDS = ["find", "insert", "erase", "mixed", "evict", "maint", "split", "merge", "count"]
+           "hive_reserve", "hive_memory", "hive_last_error",
+           "hive32_config_default", "hive32_create", "hive32_destroy", "hive32_insert",
+           "hive32_find", "hive32_erase", "hive32_execute", "hive32_size", "hive32_clear",
+           "hive32_check",
+           "hive32_stats", "hive32_dump"]
+KERNEL_KINDS = ["find", "insert", "erase", "mixed", "evict", "maint", "split", "merge", "count",
+                "fused"]
 
 
 class HiveError(RuntimeError):
@@ -56,7 +61,7 @@ class Stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "replaced", "claimed_fast", "overflowed", "claimed_slow", "evict_rounds", "lock_acquired",
         "lock_timeouts", "stashed", "pending", "stash_reinserted", "splits", "merges", "probes",
-        "stash_lookups")]
+        "stash_lookups", "fused_retries")]
 
 
 class Profile(C.Structure):
@@ -67,6 +72,18 @@ class Segment(C.Structure):
     _fields_ = [("table", C.c_uint32), ("reserved0", C.c_uint32), ("n", C.c_uint64),
                 ("n_insert", C.c_uint64), ("ops", C.c_void_p), ("keys", C.c_void_p),
                 ("vals", C.c_void_p), ("vals_out", C.c_void_p), ("status", C.c_void_p)]
+
+
+class Config32(C.Structure):
+    _fields_ = [("slots", C.c_uint64), ("layout", C.c_uint32), ("max_evictions", C.c_uint32),
+                ("stash_permille", C.c_uint32), ("lock_spin_limit", C.c_uint32)]
+
+
+class Image32(C.Structure):
+    _fields_ = [("nb", C.c_uint64), ("M", C.c_uint32), ("p", C.c_uint32), ("layout", C.c_uint32),
+                ("buckets", C.c_void_p), ("masks", C.c_void_p), ("locks", C.c_void_p),
+                ("stash", C.c_void_p), ("stash_n", C.c_uint64), ("stash_cap", C.c_uint64),
+                ("size", C.c_uint64), ("pending", C.c_uint64)]
 
 
 class Image(C.Structure):
@@ -100,6 +117,7 @@ def load_library(path: str = LIB_PATH):
         L.hive_find.argtypes = [vp, vp, u64, vp, vp, vp]
         L.hive_erase.argtypes = [vp, vp, u64, vp, vp]
         L.hive_execute.argtypes = [vp, vp, vp, vp, u64, vp, vp, vp]
+        L.hive_execute_fused.argtypes = [vp, vp, vp, vp, u64, vp, vp, vp]
         L.hive_size.argtypes = [vp, C.POINTER(u64), vp]
         L.hive_capacity.argtypes = [vp, C.POINTER(u64)]
         L.hive_reserve.argtypes = [vp, u64, vp]
@@ -118,10 +136,23 @@ def load_library(path: str = LIB_PATH):
         L.hive_multi_destroy.argtypes = [vp]
         L.hive_profile_enable.argtypes = [vp, i32]
         L.hive_profile_read.argtypes = [vp, C.POINTER(Profile)]
+        L.hive32_config_default.argtypes = [C.POINTER(Config32)]
+        L.hive32_config_default.restype = None
+        L.hive32_create.argtypes = [C.POINTER(Config32), vp, C.POINTER(vp)]
+        L.hive32_destroy.argtypes = [vp]
+        L.hive32_insert.argtypes = [vp, vp, vp, u64, vp, vp]
+        L.hive32_find.argtypes = [vp, vp, u64, vp, vp, vp]
+        L.hive32_erase.argtypes = [vp, vp, u64, vp, vp]
+        L.hive32_execute.argtypes = [vp, vp, vp, vp, u64, vp, vp, vp]
+        L.hive32_size.argtypes = [vp, C.POINTER(u64), vp]
+        L.hive32_check.argtypes = [vp, vp]
+        L.hive32_clear.argtypes = [vp, vp]
+        L.hive32_stats.argtypes = [vp, C.POINTER(Stats), vp]
+        L.hive32_dump.argtypes = [vp, C.POINTER(Image32), vp]
         L.hive_last_error.argtypes = []
         L.hive_last_error.restype = C.c_char_p
         for name in EXPORTS:
-            if name not in ("hive_config_default", "hive_last_error"):
+            if name not in ("hive_config_default", "hive_last_error", "hive32_config_default"):
                 getattr(L, name).restype = i32
         _lib = L
         return L
@@ -264,13 +295,15 @@ class HiveTable:
             self._h, _dptr(keys, 4, n, "keys"), n, _dptr(st, 1, n, "status"), _stream_ptr(stream)))
         return st
 
-    def execute(self, ops, keys, vals=None, stream=None):
-        """Mixed batch.  Returns (values, status)."""
+    def execute(self, ops, keys, vals=None, stream=None, fused=False):
+        """Mixed batch.  Returns (values, status).  fused=True runs it as one
+        concurrent kernel (hive_execute_fused) instead of the phased launches."""
         torch = _torch()
         n = keys.numel()
         vo = torch.empty(n, dtype=keys.dtype, device=keys.device)
         st = torch.empty(n, dtype=torch.uint8, device=keys.device)
-        _raise(self._L, self._L.hive_execute(
+        fn = self._L.hive_execute_fused if fused else self._L.hive_execute
+        _raise(self._L, fn(
             self._h, _dptr(ops, 1, n, "ops"), _dptr(keys, 4, n, "keys"),
             _dptr(vals, 4, n, "vals") if vals is not None else None, n,
             _dptr(vo, 4, n, "vals_out"), _dptr(st, 1, n, "status"), _stream_ptr(stream)))
@@ -369,6 +402,118 @@ class HiveTable:
         return {"nb": nb, "S": S, "M": int(img.M), "p": int(img.p), "buckets": b, "masks": m,
                 "locks": lk, "stash": st[: int(img.stash_n)], "stash_cap": int(img.stash_cap),
                 "size": int(img.size), "pending": int(img.pending)}
+
+
+KEY16_VAL16, KEY_ONLY = 0, 1
+
+
+class Hive32Table:
+    """A fixed-capacity table with 32-bit entries (hive32_*): a 16-bit key with
+    a 16-bit value (layout KEY16_VAL16) or a set of 32-bit keys (KEY_ONLY);
+    32 slots of 4 bytes per 128-byte bucket."""
+
+    def __init__(self, slots: int = 1 << 20, layout: int = KEY16_VAL16, *, max_evictions: int = 16,
+                 stash_permille: int = 10, lock_spin_limit: int | None = None, stream=None):
+        self._L = load_library()
+        cfg = Config32()
+        self._L.hive32_config_default(C.byref(cfg))
+        cfg.slots = int(slots)
+        cfg.layout = int(layout)
+        cfg.max_evictions = int(max_evictions)
+        cfg.stash_permille = int(stash_permille)
+        if lock_spin_limit is not None:
+            cfg.lock_spin_limit = int(lock_spin_limit)
+        self.config = cfg
+        h = C.c_void_p()
+        _raise(self._L, self._L.hive32_create(C.byref(cfg), _stream_ptr(stream), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.hive32_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def insert(self, keys, vals=None, status=True, stream=None):
+        torch = _torch()
+        n = keys.numel()
+        st = torch.empty(n, dtype=torch.uint8, device=keys.device) if status is True else (
+            status if status is not None and status is not False else None)
+        _raise(self._L, self._L.hive32_insert(
+            self._h, _dptr(keys, 4, n, "keys"), _dptr(vals, 4, n, "vals"), n,
+            _dptr(st, 1, n, "status"), _stream_ptr(stream)))
+        return st
+
+    def find(self, keys, vals_out=None, found=True, stream=None):
+        torch = _torch()
+        n = keys.numel()
+        if vals_out is None:
+            vals_out = torch.empty(n, dtype=keys.dtype, device=keys.device)
+        fo = torch.empty(n, dtype=torch.uint8, device=keys.device) if found is True else (
+            found if found is not None and found is not False else None)
+        _raise(self._L, self._L.hive32_find(
+            self._h, _dptr(keys, 4, n, "keys"), n, _dptr(vals_out, 4, n, "vals_out"),
+            _dptr(fo, 1, n, "found"), _stream_ptr(stream)))
+        return vals_out, fo
+
+    def erase(self, keys, status=True, stream=None):
+        torch = _torch()
+        n = keys.numel()
+        st = torch.empty(n, dtype=torch.uint8, device=keys.device) if status is True else (
+            status if status is not None and status is not False else None)
+        _raise(self._L, self._L.hive32_erase(
+            self._h, _dptr(keys, 4, n, "keys"), n, _dptr(st, 1, n, "status"), _stream_ptr(stream)))
+        return st
+
+    def execute(self, ops, keys, vals=None, stream=None):
+        torch = _torch()
+        n = keys.numel()
+        vo = torch.empty(n, dtype=keys.dtype, device=keys.device)
+        st = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        _raise(self._L, self._L.hive32_execute(
+            self._h, _dptr(ops, 1, n, "ops"), _dptr(keys, 4, n, "keys"),
+            _dptr(vals, 4, n, "vals") if vals is not None else None, n,
+            _dptr(vo, 4, n, "vals_out"), _dptr(st, 1, n, "status"), _stream_ptr(stream)))
+        return vo, st
+
+    def size(self, stream=None) -> int:
+        out = C.c_uint64()
+        _raise(self._L, self._L.hive32_size(self._h, C.byref(out), _stream_ptr(stream)))
+        return int(out.value)
+
+    def check(self, stream=None) -> int:
+        return int(self._L.hive32_check(self._h, _stream_ptr(stream)))
+
+    def clear(self, stream=None):
+        _raise(self._L, self._L.hive32_clear(self._h, _stream_ptr(stream)))
+
+    def stats(self, stream=None) -> dict:
+        s = Stats()
+        _raise(self._L, self._L.hive32_stats(self._h, C.byref(s), _stream_ptr(stream)))
+        return {f: int(getattr(s, f)) for f, _ in Stats._fields_}
+
+    def dump(self, stream=None) -> dict:
+        img = Image32()
+        _raise(self._L, self._L.hive32_dump(self._h, C.byref(img), _stream_ptr(stream)))
+        nb = int(img.nb)
+        b = np.empty(nb * 32, np.uint32)
+        m = np.empty(nb, np.uint32)
+        lk = np.empty(nb, np.uint32)
+        st = np.empty(max(int(img.stash_n), 1), np.uint32)
+        img.buckets = b.ctypes.data
+        img.masks = m.ctypes.data
+        img.locks = lk.ctypes.data
+        img.stash = st.ctypes.data
+        _raise(self._L, self._L.hive32_dump(self._h, C.byref(img), _stream_ptr(stream)))
+        return {"nb": nb, "S": 32, "M": int(img.M), "p": int(img.p), "layout": int(img.layout),
+                "buckets": b, "masks": m, "locks": lk, "stash": st[: int(img.stash_n)],
+                "stash_cap": int(img.stash_cap), "size": int(img.size),
+                "pending": int(img.pending)}
 
 
 class HiveMulti:

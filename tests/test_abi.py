@@ -16,7 +16,7 @@ def _declared():
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"\b(hive_[a-z0-9_]+)\s*\(", src))
+            names |= set(re.findall(r"\b(hive(?:32)?_[a-z0-9_]+)\s*\(", src))
     return names
 
 
