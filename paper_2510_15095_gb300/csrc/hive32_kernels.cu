@@ -30,6 +30,11 @@ constexpr int kStage32BytesPerWarp = 4 * kStage32Words + 16;
 constexpr size_t kStage32Smem = static_cast<size_t>(kOps32Threads / 32) * kStage32BytesPerWarp;
 constexpr uint32_t kMbarSpin32 = 1u << 22;
 constexpr int kMaint32Threads = 1024;
+#ifndef HIVE32_STAGE_LSU
+// Staged rounds copy buckets with cp.async through the load/store path (1)
+// or with one bulk copy (TMA) per bucket (0).
+#define HIVE32_STAGE_LSU 1
+#endif
 constexpr unsigned kMaint32SmemWords = 16384;  // 64 KB of words sorted in shared memory
 
 // Entry layouts.
@@ -122,6 +127,27 @@ template <bool PAIR>
 __device__ __forceinline__ bool stage32_round(const View32& v, Stage32& sg, unsigned need,
                                               uint32_t x1, uint32_t x2, int lane) {
   constexpr uint32_t kBucketBytes = kS32 * 4u;
+  if (HIVE32_STAGE_LSU) {
+    // cp.async through the load/store path: eight lanes copy one 128-byte
+    // bucket, 16 bytes each, so one warp instruction moves four buckets
+    constexpr int NB = PAIR ? 64 : 32;
+    const int q = lane >> 3, ql = lane & 7;
+    __syncwarp();
+#pragma unroll 4
+    for (int r = 0; r < NB / 4; ++r) {
+      const int bi = 4 * r + q;
+      const int op = PAIR ? (bi >> 1) : bi;
+      const uint32_t y1 = __shfl_sync(kFull, x1, op);
+      const uint32_t y2 = PAIR ? __shfl_sync(kFull, x2, op) : 0u;
+      const uint32_t b = (PAIR && (bi & 1)) ? y2 : y1;
+      if ((need >> op) & 1u)
+        cp_async16(sg.buf + bi * kS32 + 4 * ql, v.buckets + static_cast<uint64_t>(b) * kS32 + 4 * ql);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncwarp();
+    return true;
+  }
   fence_proxy_async();
   __syncwarp();
   if (lane == 0) mbar_arrive_expect_tx(sg.bar, __popc(need) * (PAIR ? 2u : 1u) * kBucketBytes);

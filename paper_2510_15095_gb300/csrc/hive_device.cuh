@@ -119,6 +119,18 @@ __device__ __forceinline__ void fence_proxy_async() {
 __device__ __forceinline__ void lds_frag(const uint64_t* p, uint64_t& a, uint64_t& b) {
   asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(smem_u32(p)));
 }
+// Ampere-style asynchronous 16-byte copy global -> shared through the
+// load/store path (L1 bypassed), and its group commit / wait.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
 __device__ __forceinline__ uint32_t ld_acquire32(const uint32_t* p) {
   uint32_t r;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");

@@ -36,19 +36,25 @@ constexpr int kOpsThreads = 256;
 // Bulk-kernel modes (bit kModeFind, kModeInsert, ...) whose probes are staged
 // in shared memory by bulk copies, per bucket width; the others load
 // fragments straight from global memory with the warp-wide match-and-elect.
-// Measured on the 2^26-slot, 95%-load bench workload: staging wins for
-// insert, erase and mixed batches at both widths, and for finds at S = 32
-// (18.2 against 16.4 Gops/s); S = 16 finds stay direct (29.0 against 23.4).
+// Measured on the 2^26-slot, 95%-load bench workload, staging wins for
+// every mode at both widths (with the copy path chosen below per width).
 #ifndef HIVE_STAGED_MODES_S16
-#define HIVE_STAGED_MODES_S16 0xE
+#define HIVE_STAGED_MODES_S16 0xF
 #endif
 #ifndef HIVE_STAGED_MODES_S32
 #define HIVE_STAGED_MODES_S32 0xF
 #endif
-#ifndef HIVE_PAIRED_ANY
-// Staged erase and mixed batches copy both candidate buckets of every op in
-// one round instead of one bucket per round.
-#define HIVE_PAIRED_ANY 0
+// How a staged round copies its buckets, per bucket width: 1 = cp.async
+// through the load/store path (16 bytes per lane, coalesced per bucket),
+// 0 = one bulk copy (TMA) per bucket.  Measured on the bench workload, the
+// load/store path wins for 128-byte buckets (S = 16 finds 30.1 against 27.7
+// Gops/s) and bulk copies win for 256-byte buckets (S = 32 inserts 11.7
+// against 11.0).
+#ifndef HIVE_STAGE_LSU_S16
+#define HIVE_STAGE_LSU_S16 1
+#endif
+#ifndef HIVE_STAGE_LSU_S32
+#define HIVE_STAGE_LSU_S32 0
 #endif
 #ifndef HIVE_STAGED_MIN_BLOCKS
 #define HIVE_STAGED_MIN_BLOCKS 3  // 64 KB of staging per block: three blocks fit an SM
@@ -240,7 +246,7 @@ __device__ __forceinline__ void stage_drain(Stage& sg) {
 // of their lanes to buffer buckets 2 (j - o0) and 2 (j - o0) + 1.  Returns
 // false, with the stage marked dead and the error raised, if the wait gave up.
 template <int S, bool PAIR>
-__device__ __forceinline__ bool stage_round(const View& v, Stage& sg, unsigned need, int o0,
+__device__ __forceinline__ void stage_issue(const View& v, Stage& sg, unsigned need, int o0,
                                             uint32_t x1, uint32_t x2, int lane) {
   constexpr uint32_t kBucketBytes = S * 8u;
   fence_proxy_async();  // earlier fragment reads of the buffer come before the new copies
@@ -263,6 +269,10 @@ __device__ __forceinline__ bool stage_round(const View& v, Stage& sg, unsigned n
                  kBucketBytes, sg.bar);
     }
   }
+}
+
+// Waits (bounded, warp-wide) for the copies of the round issued last.
+__device__ __forceinline__ bool stage_wait(const View& v, Stage& sg, int lane) {
   bool ok = false;
   for (uint32_t it = 0; it < kMbarSpinLimit && !ok; ++it) ok = mbar_try_wait(sg.bar, sg.phase);
   sg.phase ^= 1u;
@@ -272,6 +282,47 @@ __device__ __forceinline__ bool stage_round(const View& v, Stage& sg, unsigned n
     return false;
   }
   return true;
+}
+
+// The same round through the load/store path: the lanes of a group of L = S/2
+// copy one bucket with 16-byte cp.async each, so one warp instruction moves
+// 32 / L whole buckets, coalesced exactly as the direct probe loads them.
+// stage_wait_lsu() then waits for the warp's copies (cp.async.wait_group)
+// and syncs the warp.  No registers hold the data and no spin loop waits.
+template <int S, bool PAIR>
+__device__ __forceinline__ void stage_issue_lsu(const View& v, Stage& sg, unsigned need, int o0,
+                                                uint32_t x1, uint32_t x2, int lane) {
+  constexpr int L = Geo<S>::L, Q = Geo<S>::Q;  // lanes per bucket, buckets per instruction
+  constexpr int NB = PAIR ? 2 * (kStageWords / (2 * S)) : 32;  // buckets per round
+  const int q = lane / L, ql = lane % L;
+  __syncwarp();  // earlier reads of the buffer by any lane come first
+#pragma unroll 4
+  for (int r = 0; r < NB / Q; ++r) {
+    const int bi = Q * r + q;                  // buffer bucket of this lane group
+    const int op = PAIR ? o0 + (bi >> 1) : bi;  // its op
+    const uint32_t y1 = __shfl_sync(kFull, x1, op & 31);
+    const uint32_t y2 = PAIR ? __shfl_sync(kFull, x2, op & 31) : 0u;
+    const uint32_t b = (PAIR && (bi & 1)) ? y2 : y1;
+    if ((need >> op) & 1u)
+      cp_async16(sg.buf + bi * S + 2 * ql, v.buckets + static_cast<uint64_t>(b) * S + 2 * ql);
+  }
+  cp_async_commit();
+}
+__device__ __forceinline__ void stage_wait_lsu() {
+  cp_async_wait_all();
+  __syncwarp();
+}
+
+template <int S, bool PAIR>
+__device__ __forceinline__ bool stage_round(const View& v, Stage& sg, unsigned need, int o0,
+                                            uint32_t x1, uint32_t x2, int lane) {
+  if (S == 16 ? HIVE_STAGE_LSU_S16 : HIVE_STAGE_LSU_S32) {
+    stage_issue_lsu<S, PAIR>(v, sg, need, o0, x1, x2, lane);
+    stage_wait_lsu();
+    return true;
+  }
+  stage_issue<S, PAIR>(v, sg, need, o0, x1, x2, lane);
+  return stage_wait(v, sg, lane);
 }
 
 // One probe round over the 32 ops of a warp.  `need` has bit j set when op j
@@ -579,114 +630,6 @@ __device__ __forceinline__ void probe_round(const View& v, unsigned need, uint32
   probe<MODE, S>(v, need, myb, key, val, op, lane, done, st, outv, fcnt, fslot, cnt, unused);
 }
 
-// Erase and mixed batches, staged: both candidate buckets of every op are
-// copied in one round (a probe round trip instead of two), and each lane
-// scans its op's two buckets in BitHash1-then-BitHash2 order and acts on the
-// first match exactly as probe() does.  Reading the BitHash2 bucket of an op
-// that hits in its BitHash1 bucket is speculative: it costs bytes, which these
-// latency-bound batches have to spare, and is not counted as a probe.
-// Returns the probes the op needed (1 on a BitHash1 hit, else 2).
-template <int MODE, int S>
-__device__ __forceinline__ uint32_t scan_staged_any(const View& v, const uint64_t* sbuf, int jj,
-                                                    uint32_t b1, uint32_t b2, uint32_t key,
-                                                    uint32_t val, uint32_t op, uint32_t m1,
-                                                    uint32_t m2, bool& done, uint8_t& st,
-                                                    uint32_t& outv, uint32_t& f1, uint32_t& s1,
-                                                    uint32_t& f2, uint32_t& s2,
-                                                    LaneCounters& cnt) {
-  constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
-  constexpr int NP = S / 2;
-  const uint64_t* B = sbuf + 2 * jj * S;
-  int ms = -1;
-#pragma unroll
-  for (int which = 0; which < 2; ++which) {
-    if (ms >= 0) break;
-#pragma unroll 8
-    for (int k = 0; k < NP; ++k) {
-      const int f = (k + jj) & (NP - 1);
-      uint64_t a, b;
-      lds_frag(B + which * S + 2 * f, a, b);
-      if (key_of(a) == key) ms = which * S + 2 * f;
-      if (key_of(b) == key) ms = which * S + 2 * f + 1;
-    }
-  }
-  if (ms >= 0) {
-    done = true;
-    const uint64_t cur = B[ms];
-    const uint32_t b = ms < S ? b1 : b2;
-    const uint32_t slot = ms & (S - 1);
-    const uint32_t opk = MODE == kModeMixed ? op : (MODE == kModeErase ? OP_ERASE : OP_FIND);
-    if (opk == OP_FIND) {
-      outv = val_of(cur);
-      st = ST_FOUND;
-    } else {
-      uint64_t* sp = v.buckets + static_cast<uint64_t>(b) * S + slot;
-      if (opk == OP_ERASE) {
-        st = ST_ERASED;
-        if (atomicCAS(ull(sp), cur, kEmptyWord) == cur) {
-          atomicOr(v.masks + b, 1u << slot);
-          cnt.size_delta -= 1;
-        } else {
-          cnt.contract = true;
-        }
-      } else {
-        st = ST_REPLACED;
-        if (atomicCAS(ull(sp), cur, pack(key, val)) == cur)
-          cnt.replaced += 1;
-        else
-          cnt.contract = true;
-      }
-    }
-    return ms < S ? 1u : 2u;
-  }
-  if (kIns) {
-    f1 = __popc(m1);
-    f2 = __popc(m2);
-    s1 = m1 ? __ffs(m1) - 1 : S;
-    s2 = m2 ? __ffs(m2) - 1 : S;
-  }
-  return 2u;
-}
-
-// The paired staged round of erase and mixed batches, in batches of 512 / S
-// ops.  A stage that has given up falls back to the two direct rounds.
-template <int MODE, int S>
-__device__ __forceinline__ void probe_any_paired(const View& v, unsigned need, uint32_t b1,
-                                                 uint32_t b2, uint32_t key, uint32_t val,
-                                                 uint32_t op, int lane, bool& done, uint8_t& st,
-                                                 uint32_t& outv, uint32_t& f1, uint32_t& s1,
-                                                 uint32_t& f2, uint32_t& s2, LaneCounters& cnt,
-                                                 Stage* sg) {
-  constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
-  constexpr int BO = kStageWords / (2 * S);
-  constexpr unsigned BM = (BO >= 32) ? 0xFFFFFFFFu : ((1u << BO) - 1u);
-  const bool mine = (need >> lane) & 1u;
-  const bool ins = kIns && mine && op == OP_INSERT;
-  const uint32_t m1 = ins ? ld_relaxed32(v.masks + b1) : 0u;
-  const uint32_t m2 = ins ? ld_relaxed32(v.masks + b2) : 0u;
-  uint32_t probes = 0;
-  unsigned rest = need;
-#pragma unroll 1
-  for (int o0 = 0; o0 < 32 && !sg->dead; o0 += BO) {
-    const unsigned bneed = need & (BM << o0);
-    if (!bneed) continue;
-    if (!stage_round<S, true>(v, *sg, bneed, o0, b1, b2, lane)) break;
-    rest &= ~bneed;
-    if ((bneed >> lane) & 1u)
-      probes = scan_staged_any<MODE, S>(v, sg->buf, lane - o0, b1, b2, key, val, op, m1, m2, done,
-                                        st, outv, f1, s1, f2, s2, cnt);
-  }
-  cnt.probes += __reduce_add_sync(kFull, probes);
-  if (rest) {  // a staged wait gave up: the rest of the ops probe directly
-    bool unused = false;
-    cnt.probes += __popc(rest);
-    probe<MODE, S>(v, rest, b1, key, val, op, lane, done, st, outv, f1, s1, cnt, unused);
-    rest = __ballot_sync(kFull, ((rest >> lane) & 1u) && !done);
-    cnt.probes += __popc(rest);
-    if (rest) probe<MODE, S>(v, rest, b2, key, val, op, lane, done, st, outv, f2, s2, cnt, unused);
-  }
-}
-
 // The paired insert round on staged buckets, one op per lane.  With both
 // candidate buckets of its op in shared memory, a lane scans them itself:
 // S / 2 16-byte fragment reads per bucket, starting at fragment (op mod S / 2)
@@ -858,10 +801,6 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
   if (MODE == kModeInsert) {
     cnt.probes += 2 * __popc(need);
     if (need) probe_pair_round<S>(v, need, b1, b2, key, val, lane, done, st, f1, s1, f2, s2, cnt, sg);
-  } else if ((MODE == kModeErase || MODE == kModeMixed) && HIVE_PAIRED_ANY && sg) {
-    if (need)
-      probe_any_paired<MODE, S>(v, need, b1, b2, key, val, op, lane, done, st, outv, f1, s1, f2,
-                                s2, cnt, sg);
   } else {
     cnt.probes += __popc(need);
     if (need) probe_round<MODE, S>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt, sg);
