@@ -120,10 +120,20 @@ __device__ __forceinline__ void lds_frag(const uint64_t* p, uint64_t& a, uint64_
   asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(smem_u32(p)));
 }
 // Ampere-style asynchronous 16-byte copy global -> shared through the
-// load/store path (L1 bypassed), and its group commit / wait.
+// load/store path, and its group commit / wait.  HIVE_CP_ASYNC_L1 selects
+// the L1-caching form (.ca) over the L2-only form (.cg): with Zipf-skewed
+// lookups the hot buckets are then served from L1 (measured: Zipf(0.99) finds
+// 38.8 against 21.3 Gops/s, uniform finds 31.3 against 29.3).
+#ifndef HIVE_CP_ASYNC_L1
+#define HIVE_CP_ASYNC_L1 1
+#endif
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
-               : "memory");
+  if (HIVE_CP_ASYNC_L1)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;" ::: "memory");

@@ -55,6 +55,12 @@ hive_status cuda_fail(cudaError_t e, const char* what) {
 
 constexpr uint64_t kMaxBuckets = 1ull << 31;
 
+// Resizable tables map their buckets on demand through CUDA virtual memory
+// (1) or allocate max_slots up front (0).
+#ifndef HIVE_VMM_TABLES
+#define HIVE_VMM_TABLES 1
+#endif
+
 uint64_t next_pow2(uint64_t x) {
   uint64_t p = 1;
   while (p < x) p <<= 1;
@@ -457,7 +463,7 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
     t->L.ops_blocks_per_sm = std::min(t->L.ops_blocks_per_sm, cap);
     t->L.staged_blocks_per_sm = std::min(t->L.staged_blocks_per_sm, cap);
   }
-  if (e == cudaSuccess && cfg->resizable) {
+  if (e == cudaSuccess && cfg->resizable && HIVE_VMM_TABLES) {
     // reserve the address range of nb_max buckets, back only nb_init of them
     if (grow_reserve(&t->bucket_vm, t->nb_max * S * sizeof(uint64_t), t->device) == cudaSuccess) {
       t->vmm = true;

@@ -196,7 +196,8 @@ struct GrowArray {
   uint64_t base = 0;
   size_t reserved = 0, committed = 0, gran = 0;
   int device = 0;
-  std::vector<uint64_t> handles;  // one physical allocation per chunk
+  std::vector<uint64_t> handles;  // physical allocations, mapped back to back from base
+  std::vector<size_t> sizes;      // bytes of each
 };
 cudaError_t grow_reserve(GrowArray* a, size_t max_bytes, int device);
 cudaError_t grow_commit(GrowArray* a, size_t bytes, cudaStream_t s);  // new chunks filled 0xFF

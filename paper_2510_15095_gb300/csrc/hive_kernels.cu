@@ -1,25 +1,32 @@
 // Hive hash table kernels for GB300 (sm_103a).
 //
-// Layout (Section III-A/B of the paper): a bucket is S = 32 packed 64-bit words
-// (value << 32 | key), 256 bytes, 256-byte aligned; a 32-bit free mask per bucket
-// (bit i set = slot i free); a 32-bit lock per bucket used only by eviction; an
-// overflow stash of packed words.  The empty word is all ones (key 0xFFFFFFFF).
+// Layout (Section III-A/B of the paper): a bucket is S packed 64-bit words
+// (value << 32 | key), S = 32 (256 bytes) or 16 (128 bytes), aligned to its
+// size; a 32-bit free mask per bucket (bit i set = slot i free); a 32-bit lock
+// per bucket used only by eviction; an overflow stash of packed words.  The
+// empty word is all ones (key 0xFFFFFFFF).
 //
 // Kernels:
-//   k_ops<MODE>   bulk find / insert (steps 1-2) / erase / mixed batch.  A warp
-//                 takes 32 ops; each 16-lane half-warp reads one 256-byte bucket
-//                 as 16-byte fragments, so one load instruction probes two
-//                 buckets.  Match-and-elect (WCME, Section III-F) is a ballot over
-//                 the fragments; the lowest matching lane acts.  New keys claim
-//                 a slot with one atomicAnd on the free mask (WABC, Section
-//                 III-E), the free slot being predicted from the probe itself.
-//   k_overflow    steps 3-4 for inserts whose two buckets were full: warp per
-//                 item, bounded cuckoo eviction under the bucket lock
-//                 (Algorithm 3), then the stash.
-//   k_maint       stash maintenance: reinsert stash words into buckets that
-//                 have room, compact, sort by key (lookups binary-search it).
-//   k_split       linear-hashing expansion, warp per bucket pair (Section IV-C1).
-//   k_merge       linear-hashing contraction, warp per bucket pair (IV-C2).
+//   k_ops<MODE,S>  bulk find / insert (steps 1-2) / erase / mixed batch.  A
+//                  warp takes 32 ops.  Staged: each probe round copies the
+//                  buckets of all 32 ops into the warp's shared-memory buffer
+//                  (cp.async for 128-byte buckets, one bulk copy per 256-byte
+//                  bucket) and each lane scans its own op's buckets.  Direct:
+//                  L = S/2 lanes read a bucket as 16-byte fragments, and
+//                  match-and-elect (WCME, Section III-F) is a ballot over the
+//                  fragments.  New keys claim a slot with one atomicAnd on the
+//                  free mask (WABC, Section III-E), the free slot predicted from
+//                  the probe round.
+//   k_overflow<S>  steps 3-4 for inserts whose two buckets were full: warp per
+//                  item, bounded cuckoo eviction under the bucket lock
+//                  (Algorithm 3), then the stash.
+//   k_maint<S>     stash maintenance: reinsert stash words into buckets that
+//                  have room, compact, sort by key (lookups binary-search it).
+//   k_split<S>     linear-hashing expansion, warp per bucket pair (Section IV-C1).
+//   k_merge<S>     linear-hashing contraction, warp per bucket pair (IV-C2).
+//   k_fused<S>     a mixed batch as one concurrent kernel (bucket versions make
+//                  lookups safe against eviction chains in flight).
+//   k_multi_*      the same phases over many tables in one launch each.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -142,6 +149,26 @@ __device__ __forceinline__ bool claim_cas(const View& v, uint32_t b, uint64_t wo
     } else {
       fm = old;
     }
+  }
+  return false;
+}
+// The claim of the phased eviction kernel: fetch_and on the free mask, then a
+// plain store.  No CAS is needed there: in that phase slots only go from
+// EMPTY to occupied (there are no erases), and a chain exchanges only a
+// slot it saw occupied, so nothing else writes a claimed, unpublished slot.
+template <int S>
+__device__ __forceinline__ bool claim_pub(const View& v, uint32_t b, uint64_t word,
+                                          uint32_t hint = 0) {
+  uint32_t fm = hint ? hint : ld_relaxed32(v.masks + b);
+  for (int t = 0; t <= S && fm; ++t) {
+    const uint32_t s = __ffs(fm) - 1;
+    const uint32_t bit = 1u << s;
+    const uint32_t old = atomicAnd(v.masks + b, ~bit);
+    if (old & bit) {
+      st_relaxed64(v.buckets + static_cast<uint64_t>(b) * S + s, word);
+      return true;
+    }
+    fm = old;
   }
   return false;
 }
@@ -551,6 +578,33 @@ __device__ __forceinline__ void probe_pair(const View& v, unsigned need, uint32_
   }
 }
 
+// An erase or replace CAS issued by a staged probe round, checked only at the
+// end of the chunk, so that its round trip overlaps the rounds and claims
+// after it (an op updates at most one slot, so one record per lane).
+struct PendCas {
+  uint64_t cur, old;
+  uint32_t b, slot, kind;  // kind: 0 none, 1 erase, 2 replace
+};
+
+__device__ __forceinline__ void resolve_cas(const View& v, const PendCas& pc, LaneCounters& cnt) {
+  if (pc.kind == 0) return;
+  const bool ok = pc.old == pc.cur;
+  if (pc.kind == 1) {
+    // Algorithm 4: the free bit is published once the CAS has emptied the slot
+    if (ok) {
+      atomicOr(v.masks + pc.b, 1u << pc.slot);
+      cnt.size_delta -= 1;
+    } else {
+      cnt.contract = true;
+    }
+  } else {
+    if (ok)
+      cnt.replaced += 1;
+    else
+      cnt.contract = true;
+  }
+}
+
 // A single-bucket probe round on staged buckets, one op per lane: lane j
 // scans buffer bucket j (its op's bucket this round) with swizzled 16-byte
 // reads, as scan_staged_pair() below does for both buckets, and acts on a
@@ -561,7 +615,7 @@ __device__ __forceinline__ void scan_staged_one(const View& v, const uint64_t* s
                                                 uint32_t myb, uint32_t key, uint32_t val,
                                                 uint32_t op, uint32_t mask, bool& done,
                                                 uint8_t& st, uint32_t& outv, uint32_t& fcnt,
-                                                uint32_t& fslot, LaneCounters& cnt) {
+                                                uint32_t& fslot, PendCas& pc) {
   constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
   constexpr int NP = S / 2;
   const uint64_t* B = sbuf + lane * S;
@@ -586,21 +640,12 @@ __device__ __forceinline__ void scan_staged_one(const View& v, const uint64_t* s
       st = ST_FOUND;
     } else {
       uint64_t* sp = v.buckets + static_cast<uint64_t>(myb) * S + ms;
-      if (opk == OP_ERASE) {
-        st = ST_ERASED;
-        if (atomicCAS(ull(sp), cur, kEmptyWord) == cur) {
-          atomicOr(v.masks + myb, 1u << ms);
-          cnt.size_delta -= 1;
-        } else {
-          cnt.contract = true;
-        }
-      } else {
-        st = ST_REPLACED;
-        if (atomicCAS(ull(sp), cur, pack(key, val)) == cur)
-          cnt.replaced += 1;
-        else
-          cnt.contract = true;
-      }
+      st = opk == OP_ERASE ? ST_ERASED : ST_REPLACED;
+      pc.old = atomicCAS(ull(sp), cur, opk == OP_ERASE ? kEmptyWord : pack(key, val));
+      pc.cur = cur;
+      pc.b = myb;
+      pc.slot = ms;
+      pc.kind = opk == OP_ERASE ? 1u : 2u;
     }
   } else if (kIns) {
     fcnt = __popc(mask);
@@ -614,7 +659,7 @@ __device__ __forceinline__ void probe_round(const View& v, unsigned need, uint32
                                             uint32_t key, uint32_t val, uint32_t op, int lane,
                                             bool& done, uint8_t& st, uint32_t& outv,
                                             uint32_t& fcnt, uint32_t& fslot, LaneCounters& cnt,
-                                            Stage* sg) {
+                                            Stage* sg, PendCas& pc) {
   constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
   if (sg && !sg->dead) {
     const bool mine = (need >> lane) & 1u;
@@ -622,7 +667,7 @@ __device__ __forceinline__ void probe_round(const View& v, unsigned need, uint32
     if (stage_round<S, false>(v, *sg, need, 0, myb, 0, lane)) {
       if (mine)
         scan_staged_one<MODE, S>(v, sg->buf, lane, myb, key, val, op, m, done, st, outv, fcnt,
-                                 fslot, cnt);
+                                 fslot, pc);
       return;
     }
   }
@@ -794,6 +839,7 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
   uint8_t st = reserved ? ST_RESERVED : ST_NOT_FOUND;
   uint32_t outv = 0;
   uint32_t f1 = 0, s1 = S, f2 = 0, s2 = S;
+  PendCas pc{0, 0, 0, 0, 0};
 
   // Probe the BitHash1 bucket of every op, then the BitHash2 bucket of the
   // ops still unresolved (Section IV-B: WCME over the d = 2 candidates).
@@ -803,10 +849,12 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
     if (need) probe_pair_round<S>(v, need, b1, b2, key, val, lane, done, st, f1, s1, f2, s2, cnt, sg);
   } else {
     cnt.probes += __popc(need);
-    if (need) probe_round<MODE, S>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt, sg);
+    if (need)
+      probe_round<MODE, S>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt, sg, pc);
     need = __ballot_sync(kFull, !done);
     cnt.probes += __popc(need);
-    if (need) probe_round<MODE, S>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt, sg);
+    if (need)
+      probe_round<MODE, S>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt, sg, pc);
   }
 
   // The stash (Section IV-A step 4) holds keys that found no bucket room.
@@ -859,6 +907,8 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
       cnt.overflowed += 1;
     }
   }
+
+  resolve_cas(v, pc, cnt);
 
   // Hand full-bucket inserts to the eviction kernel (steps 3-4).
   if (kIns) {
@@ -990,11 +1040,15 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
 
   // 0: needs eviction, 1: placed, 2: stashed, 3: no room (pending)
   int outcome = 0;
+  // the BitHash1 bucket, read now for the first eviction round: most items
+  // here find both buckets still full
+  const uint64_t w0 =
+      lane < S ? ld_relaxed64(v.buckets + static_cast<uint64_t>(b1) * S + lane) : kEmptyWord;
   if (lane == 0) {
     // both free masks in one round trip; claim where a bit is free
     const uint32_t m1 = ld_relaxed32(v.masks + b1);
     const uint32_t m2 = ld_relaxed32(v.masks + b2);
-    if ((m1 && claim_cas<S>(v, b1, word0)) || (b2 != b1 && m2 && claim_cas<S>(v, b2, word0))) {
+    if ((m1 && claim_pub<S>(v, b1, word0, m1)) || (b2 != b1 && m2 && claim_pub<S>(v, b2, word0, m2))) {
       outcome = 1;
       ++oc.claim;
     } else {
@@ -1014,8 +1068,9 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
     for (uint32_t r = 0; r < v.max_evictions; ++r) {
       // Look ahead: each lane checks whether the word in its slot could move
       // to its other candidate bucket without a further eviction.
-      const uint64_t w =
-          lane < S ? ld_relaxed64(v.buckets + static_cast<uint64_t>(b) * S + lane) : kEmptyWord;
+      const uint64_t w = r == 0 ? w0
+                                : (lane < S ? ld_relaxed64(v.buckets + static_cast<uint64_t>(b) * S + lane)
+                                            : kEmptyWord);
       uint32_t am = 0;  // free mask of this word's other candidate bucket
       if (w != kEmptyWord) {
         const uint32_t k = key_of(w);
@@ -1025,12 +1080,21 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
         if (alt != b) am = ld_relaxed32(v.masks + alt);
       }
       const unsigned gm = __ballot_sync(kFull, am != 0u);
+      const unsigned occ = __ballot_sync(kFull, lane < S && w != kEmptyWord);
       const bool has_empty = __ballot_sync(kFull, lane < S && w == kEmptyWord) != 0u;
-      int res = 0;  // 0: evicted `victim`, 1: placed, 2: lock wait gave up
+      int res = 0;  // 0: evicted `victim`, 1: placed, 2: lock wait gave up, 3: redo the round
       uint64_t victim = kEmptyWord;
-      const uint32_t vs = gm ? static_cast<uint32_t>(__ffs(gm) - 1)
-                             : ((bithash2(key_of(cur)) + r) & (S - 1));
-      const uint32_t vmask = __shfl_sync(kFull, am, vs);
+      // victim: an occupied slot whose word can move on at once, else an
+      // occupied slot picked by rotation (never an EMPTY one, see claim_pub)
+      uint32_t vs = S;
+      if (gm) {
+        vs = __ffs(gm) - 1;
+      } else if (occ) {
+        const uint32_t start = (bithash2(key_of(cur)) + r) & (S - 1);
+        const unsigned rot = (occ >> start) | (start ? (occ << (32 - start)) : 0u);
+        vs = (start + __ffs(rot) - 1) & 31;
+      }
+      const uint32_t vmask = __shfl_sync(kFull, am, vs & 31);
       if (lane == 0) {
         ++oc.rounds;
         if (!lock_bucket(v, b)) {
@@ -1038,10 +1102,10 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
           ++oc.to;
         } else {
           ++oc.locks;
-          // a free slot shows as an EMPTY word (a claimed, unpublished one
-          // too: the exchange below then reads EMPTY and stops)
-          if (has_empty && claim_cas<S>(v, b, cur)) {
+          if (has_empty && claim_pub<S>(v, b, cur)) {
             res = 1;
+          } else if (vs >= S) {
+            res = 3;  // every slot claimed but not yet published: look again
           } else {
             victim = atomicExch(ull(v.buckets + static_cast<uint64_t>(b) * S + vs), cur);
             res = (victim == kEmptyWord) ? 1 : 0;
@@ -1056,6 +1120,7 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
         break;
       }
       if (res == 2) break;
+      if (res == 3) continue;
       // Re-route the displaced word to its alternate bucket.
       cur = victim;
       const uint32_t kc = key_of(cur);
@@ -1065,7 +1130,7 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
       if (nb == b) break;  // both candidates are this bucket: no alternative
       b = nb;
       int ok = 0;
-      if (lane == 0) ok = claim_cas<S>(v, b, cur, vmask);
+      if (lane == 0) ok = claim_pub<S>(v, b, cur, vmask);
       if (__shfl_sync(kFull, ok, 0)) {
         placed = true;
         break;

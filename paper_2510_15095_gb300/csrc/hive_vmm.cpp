@@ -9,6 +9,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "hive_internal.h"
@@ -87,43 +88,51 @@ cudaError_t grow_reserve(GrowArray* a, size_t max_bytes, int device) {
   return cudaSuccess;
 }
 
+// Maps at least `bytes` (rounded up to the granularity). Growth maps one
+// physical allocation per call, of at least a quarter of what is already
+// mapped, so that a table growing step by step makes few driver calls.
 cudaError_t grow_commit(GrowArray* a, size_t bytes, cudaStream_t s) {
   const DriverVmm& d = vmm();
-  const size_t want = std::min(a->reserved, (bytes + a->gran - 1) / a->gran * a->gran);
+  const size_t g = a->gran;
+  const size_t want = std::min(a->reserved, (bytes + g - 1) / g * g);
+  if (a->committed >= want) return cudaSuccess;
+  size_t delta = want - a->committed;
+  const size_t step = (a->committed / 4 + g - 1) / g * g;
+  delta = std::min(a->reserved - a->committed, std::max(delta, step));
   const CUmemAllocationProp p = prop_for(a->device);
   CUmemAccessDesc acc{};
   acc.location = p.location;
   acc.flags = CU_MEM_ACCESS_FLAGS_PROT_READWRITE;
-  while (a->committed < want) {
-    CUmemGenericAllocationHandle h = 0;
-    if (d.create(&h, a->gran, &p, 0) != CUDA_SUCCESS) return cudaErrorMemoryAllocation;
-    const CUdeviceptr at = a->base + a->committed;
-    if (d.map(at, a->gran, 0, h, 0) != CUDA_SUCCESS) {
-      d.release(h);
-      return cudaErrorMemoryAllocation;
-    }
-    if (d.set_access(at, a->gran, &acc, 1) != CUDA_SUCCESS) {
-      d.unmap(at, a->gran);
-      d.release(h);
-      return cudaErrorMemoryAllocation;
-    }
-    a->handles.push_back(h);
-    // new buckets start empty (all-ones words)
-    cudaError_t e = cudaMemsetAsync(reinterpret_cast<void*>(at), 0xFF, a->gran, s);
-    if (e != cudaSuccess) return e;
-    a->committed += a->gran;
+  CUmemGenericAllocationHandle h = 0;
+  if (d.create(&h, delta, &p, 0) != CUDA_SUCCESS) return cudaErrorMemoryAllocation;
+  const CUdeviceptr at = a->base + a->committed;
+  if (d.map(at, delta, 0, h, 0) != CUDA_SUCCESS) {
+    d.release(h);
+    return cudaErrorMemoryAllocation;
   }
-  return cudaSuccess;
+  if (d.set_access(at, delta, &acc, 1) != CUDA_SUCCESS) {
+    d.unmap(at, delta);
+    d.release(h);
+    return cudaErrorMemoryAllocation;
+  }
+  a->handles.push_back(h);
+  a->sizes.push_back(delta);
+  a->committed += delta;
+  // new buckets start empty (all-ones words)
+  return cudaMemsetAsync(reinterpret_cast<void*>(at), 0xFF, delta, s);
 }
 
+// Unmaps whole allocations from the top while what stays mapped still
+// covers `bytes`.
 void grow_decommit(GrowArray* a, size_t bytes) {
   const DriverVmm& d = vmm();
-  const size_t keep = (bytes + a->gran - 1) / a->gran * a->gran;
-  while (a->committed > keep && !a->handles.empty()) {
-    a->committed -= a->gran;
-    d.unmap(a->base + a->committed, a->gran);
+  while (!a->handles.empty() && a->committed - a->sizes.back() >= bytes) {
+    const size_t sz = a->sizes.back();
+    a->committed -= sz;
+    d.unmap(a->base + a->committed, sz);
     d.release(a->handles.back());
     a->handles.pop_back();
+    a->sizes.pop_back();
   }
 }
 
