@@ -96,6 +96,12 @@ typedef struct {
   uint32_t lock_spin_limit; /* tries before a bucket-lock wait gives up */
   uint32_t blocks_per_sm;   /* resident 256-thread blocks per SM of the bulk kernel's
                                persistent grid; 0 = as many as fit (a tuning knob) */
+  uint32_t map_on_demand;   /* resizable tables: 1 = reserve the address range of
+                               max_slots and map bucket memory as the table grows
+                               (CUDA virtual memory; committed HBM follows the
+                               capacity, see hive_memory); 0 = allocate max_slots
+                               of buckets up front (default; faster on the
+                               multi-table path) */
 } hive_config;
 
 /* Per-table counters, accumulated since creation or the last hive_clear.

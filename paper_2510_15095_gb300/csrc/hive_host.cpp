@@ -55,12 +55,6 @@ hive_status cuda_fail(cudaError_t e, const char* what) {
 
 constexpr uint64_t kMaxBuckets = 1ull << 31;
 
-// Resizable tables map their buckets on demand through CUDA virtual memory
-// (1) or allocate max_slots up front (0).
-#ifndef HIVE_VMM_TABLES
-#define HIVE_VMM_TABLES 1
-#endif
-
 uint64_t next_pow2(uint64_t x) {
   uint64_t p = 1;
   while (p < x) p <<= 1;
@@ -177,8 +171,29 @@ hive_status split_step(hive_table* t, cudaStream_t s, bool* did) {
   return HIVE_OK;
 }
 
+// Buckets in use after the splits that a batch with `live` keys needs.
+uint64_t grown_nb(const hive_table* t, uint64_t live) {
+  uint64_t M = t->M, p = t->p, nb = t->nb;
+  while (over_grow(t, live, nb) && nb < t->nb_max) {
+    const uint64_t step = std::min<uint64_t>({t->cfg.resize_batch, M + 1 - p, t->nb_max - nb});
+    if (step == 0) break;
+    p += step;
+    nb += step;
+    if (p == M + 1) {
+      M = 2 * M + 1;
+      p = 0;
+    }
+  }
+  return nb;
+}
+
 // Before a batch with up to n_ins new keys.
 hive_status grow_for(hive_table* t, uint64_t n_ins, cudaStream_t s) {
+  // back every bucket the batch's splits create with one mapping call
+  if (t->vmm) {
+    const uint64_t nb = grown_nb(t, t->size_host + n_ins);
+    HIVE_CK(grow_commit(&t->bucket_vm, nb * t->S * sizeof(uint64_t), s));
+  }
   // K-pair steps of one round touch disjoint buckets and are fused into one
   // launch; the policy still advances K pairs at a time.
   bool any = false, have = false;
@@ -343,9 +358,9 @@ hive_status hive::contract_table(hive_table* t, cudaStream_t s) {
     t->size_host = t->host_ctrl->size;
     if (t->vmm) {
       // the work above has completed; buckets past nb are empty and unused,
-      // so their memory goes back (one chunk is kept to damp oscillation)
-      const size_t need = t->nb * t->S * sizeof(uint64_t) + t->bucket_vm.gran;
-      if (t->bucket_vm.committed > need + 3 * t->bucket_vm.gran) grow_decommit(&t->bucket_vm, need);
+      // so whole allocations above them go back
+      const size_t need = t->nb * t->S * sizeof(uint64_t);
+      if (t->bucket_vm.committed > need + 2 * t->bucket_vm.gran) grow_decommit(&t->bucket_vm, need);
     }
   }
   return HIVE_OK;
@@ -428,6 +443,7 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
           static_cast<uint64_t>(cfg->grow_num) * cfg->shrink_den)
     return fail(HIVE_ERR_INVALID_ARG, "need 0 <= shrink < grow <= 1");
   if (cfg->stash_permille > 1000 || cfg->placement > HIVE_PLACE_FIRST || cfg->blocks_per_sm > 64 ||
+      cfg->map_on_demand > 1 ||
       cfg->resizable > 1)
     return fail(HIVE_ERR_INVALID_ARG, "bad stash_permille, placement, resizable or blocks_per_sm");
 
@@ -463,7 +479,7 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
     t->L.ops_blocks_per_sm = std::min(t->L.ops_blocks_per_sm, cap);
     t->L.staged_blocks_per_sm = std::min(t->L.staged_blocks_per_sm, cap);
   }
-  if (e == cudaSuccess && cfg->resizable && HIVE_VMM_TABLES) {
+  if (e == cudaSuccess && cfg->resizable && cfg->map_on_demand) {
     // reserve the address range of nb_max buckets, back only nb_init of them
     if (grow_reserve(&t->bucket_vm, t->nb_max * S * sizeof(uint64_t), t->device) == cudaSuccess) {
       t->vmm = true;

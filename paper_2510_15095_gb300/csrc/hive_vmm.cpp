@@ -89,15 +89,16 @@ cudaError_t grow_reserve(GrowArray* a, size_t max_bytes, int device) {
 }
 
 // Maps at least `bytes` (rounded up to the granularity). Growth maps one
-// physical allocation per call, of at least a quarter of what is already
-// mapped, so that a table growing step by step makes few driver calls.
+// physical allocation per call, at least as large as what is already mapped
+// (the mapped size at least doubles), so that a table growing batch by batch
+// makes a logarithmic number of driver calls.
 cudaError_t grow_commit(GrowArray* a, size_t bytes, cudaStream_t s) {
   const DriverVmm& d = vmm();
   const size_t g = a->gran;
   const size_t want = std::min(a->reserved, (bytes + g - 1) / g * g);
   if (a->committed >= want) return cudaSuccess;
   size_t delta = want - a->committed;
-  const size_t step = (a->committed / 4 + g - 1) / g * g;
+  const size_t step = (a->committed + g - 1) / g * g;
   delta = std::min(a->reserved - a->committed, std::max(delta, step));
   const CUmemAllocationProp p = prop_for(a->device);
   CUmemAccessDesc acc{};

@@ -192,13 +192,14 @@ def test_mixed_batches(H, seed, bs):
     t.close()
 
 
-@pytest.mark.parametrize("bs", [32, 16])
-def test_resizable_grow_and_shrink(H, bs):
+@pytest.mark.parametrize("bs,on_demand", [(32, False), (16, False), (32, True), (16, True)])
+def test_resizable_grow_and_shrink(H, bs, on_demand):
     """Linear-hashing growth and contraction track the oracle's capacity model
-    call by call, with invariants (including the load-factor band) after each."""
+    call by call, with invariants (including the load-factor band) after each;
+    bucket memory allocated up front or mapped on demand."""
     K = 64
     t = H.HiveTable(1 << 12, max_slots=1 << 22, resizable=True, resize_batch=K, shrink=(2, 5),
-                    bucket_slots=bs)
+                    bucket_slots=bs, map_on_demand=on_demand)
     pol = oracle.Policy((1 << 12) // bs, (1 << 22) // bs, S=bs, K=K, shrink=(2, 5))
     d = oracle.Dict()
     rng = np.random.default_rng(9)
@@ -316,7 +317,8 @@ def test_resizable_memory_follows_capacity(H):
     merges: committed bucket bytes grow and shrink with the capacity inside a
     bucket range reserved once for max_slots.  (The per-batch work lists grow
     with the largest batch seen, on both counts.)"""
-    t = H.HiveTable(1 << 12, max_slots=1 << 24, resizable=True, resize_batch=1024)
+    t = H.HiveTable(1 << 12, max_slots=1 << 24, resizable=True, resize_batch=1024,
+                    map_on_demand=True)
     c0, r0 = t.memory()
     keys, _ = W.take_keys(55, 0, 1 << 21)
     vals = W.values_for(keys, 55)
