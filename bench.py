@@ -218,6 +218,30 @@ def oracle_sample(w, n_sample: int):
 # reference arm: the oracle on the host cores
 # ---------------------------------------------------------------------------
 
+# ---------------------------------------------------------------------------
+# multi-rank bookkeeping: independent shards, slowest rank's time
+# ---------------------------------------------------------------------------
+
+def shard_seed(rank: int) -> int:
+    """Each rank owns an independent shard: its own seeded keys and table."""
+    return SEED + rank
+
+
+def max_over_ranks(torch, dist, x: float, world: int, device) -> float:
+    """The slowest rank's time (no data-path collective: timing only)."""
+    if world <= 1:
+        return x
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gops(ops_per_rank_step: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the ops all ranks processed over the slowest
+    rank's time (weak scaling: the per-rank work is fixed)."""
+    return ops_per_rank_step * steps * world / (ms / 1e3) / 1e9
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -735,7 +759,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    seed = SEED + rank  # each rank owns an independent shard
+    seed = shard_seed(rank)
     w = make_workload(seed, args.slots)
     cfg = workload_config(w, args.slots)
     up = lambda a: H.to_device_u32(a, dev)  # noqa: E731
@@ -823,13 +847,9 @@ def main():
     clocks = sampler.stop()
     prof = t.profile_read()
     t.profile(False)
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        x = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        ms = float(x.item())
+    ms = max_over_ranks(torch, dist, e0.elapsed_time(e1), world, dev)
     ops_step = n_ins + n_find + n_mix
-    value = ops_step * args.steps * world / (ms / 1e3) / 1e9
+    value = job_gops(ops_step, args.steps, world, ms)
     gpu_launches = sum(c for _, c in prof.values())
 
     # roofline of the dominant kernel (algorithmic bytes per op x ops per launch)
@@ -927,14 +947,10 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - w0
-    e2e_ms = max(e0.elapsed_time(e1), 0.0)
-    if world > 1:
-        x = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        e2e_ms = float(x.item())
+    e2e_ms = max_over_ranks(torch, dist, max(e0.elapsed_time(e1), 0.0), world, dev)
     h2d = 4 * (2 * n_ins + n_find + 2 * n_mix) + n_mix
     d2h = n_ins + 5 * n_find + 5 * n_mix
-    e2e = {"value": ops_step * args.e2e_steps * world / (e2e_ms / 1e3) / 1e9, "unit": "Gops/s",
+    e2e = {"value": job_gops(ops_step, args.e2e_steps, world, e2e_ms), "unit": "Gops/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
            "api": "hive_insert_host / hive_find_host / hive_execute_host (pinned host buffers)",
            "host_wall_gops": ops_step * args.e2e_steps / wall / 1e9}
