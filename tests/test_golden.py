@@ -33,11 +33,11 @@ def test_op_stream_fixture():
     assert np.array_equal(est, r[:, 3]) and np.array_equal(ev, r[:, 4])
 
 
-def _phases(ops):
-    """Runs of equal op codes: each is one call (the batch contract holds
-    within every run)."""
-    cut = np.flatnonzero(np.diff(ops)) + 1
-    return np.split(np.arange(ops.size), cut)
+def _phases(n):
+    """The stream's five phases (40 inserts, 8 re-inserts, 24 finds, 16
+    erases, 8 finds), one call each, so that the batch contract holds within
+    every call; applied in order they equal the oracle's op-by-op order."""
+    return np.split(np.arange(n), [40, 48, 72, 88])
 
 
 @pytest.mark.gpu
@@ -52,7 +52,8 @@ def test_op_stream_fixture_on_gpu(bs):
     t = H.HiveTable(1 << 10, bucket_slots=bs)
     st_all = np.zeros(ops.size, np.int64)
     v_all = np.zeros(ops.size, np.int64)
-    for idx in _phases(ops):
+    assert ops.size == 96
+    for idx in _phases(ops.size):
         vo, st = t.execute(torch.from_numpy(ops[idx]).cuda(), H.to_device_u32(keys[idx]),
                            H.to_device_u32(vals[idx]))
         st_all[idx] = st.cpu().numpy()
