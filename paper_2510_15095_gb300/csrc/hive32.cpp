@@ -125,7 +125,7 @@ hive_status run32(hive32_table* t, int mode, const uint8_t* ops, const uint32_t*
   if (ins && (st = ensure_list32(t, n)) != HIVE_OK) return st;
   const View32 v = view32(t);
   const Ops32 a{ops, keys, vals, vals_out, found, status};
-  H32_CK(launch32_ops(mode, v, a, n, list32(t), t->num_sms * t->blocks_per_sm, s));
+  H32_CK(launch32_ops(mode, v, a, n, list32(t), t->num_sms, s));
   if (ins) H32_CK(launch32_overflow(v, list32(t), status, t->num_sms * 8, s));
   if (mode != kModeFind) H32_CK(launch32_maint(v, s));
   return HIVE_OK;

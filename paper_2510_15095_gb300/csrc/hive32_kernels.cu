@@ -26,8 +26,14 @@ constexpr int kS32 = 32;                   // slots per bucket
 constexpr uint32_t kEmpty32 = 0xFFFFFFFFu;  // empty slot
 constexpr int kOps32Threads = 256;
 constexpr int kStage32Words = 2048;         // 8 KB per warp: 64 buckets of 128 B
-constexpr int kStage32BytesPerWarp = 4 * kStage32Words + 16;
-constexpr size_t kStage32Smem = static_cast<size_t>(kOps32Threads / 32) * kStage32BytesPerWarp;
+// A paired insert round fills the 8 KB; a single-bucket round needs 32
+// buckets (4 KB), which lets four blocks share an SM.
+__host__ __device__ constexpr int stage32_words(int mode) {
+  return mode == kModeInsert ? kStage32Words : kStage32Words / 2;
+}
+__host__ __device__ constexpr size_t stage32_smem(int mode) {
+  return static_cast<size_t>(kOps32Threads / 32) * (4u * stage32_words(mode) + 16u);
+}
 constexpr uint32_t kMbarSpin32 = 1u << 22;
 constexpr int kMaint32Threads = 1024;
 #ifndef HIVE32_STAGE_LSU
@@ -102,9 +108,10 @@ struct Stage32 {
   bool dead;
 };
 
-__device__ __forceinline__ Stage32 stage32_init(uint64_t* smem, int warp_in_block, int lane) {
+__device__ __forceinline__ Stage32 stage32_init(uint64_t* smem, int warp_in_block, int lane,
+                                                int words) {
   Stage32 sg;
-  uint64_t* base = smem + static_cast<size_t>(warp_in_block) * (kStage32BytesPerWarp / 8);
+  uint64_t* base = smem + static_cast<size_t>(warp_in_block) * (words / 2 + 2);
   sg.bar = base;
   sg.buf = reinterpret_cast<uint32_t*>(base + 2);
   sg.phase = 0;
@@ -437,7 +444,7 @@ __device__ __forceinline__ void run_chunk32(const View32& v, uint32_t stash_n, c
 }
 
 template <int MODE, int LAYOUT>
-__global__ void __launch_bounds__(kOps32Threads, 3)
+__global__ void __launch_bounds__(kOps32Threads, MODE == kModeInsert ? 3 : 4)
     k32_ops(View32 v, Ops32 a, uint64_t n, List32 ovf) {
   extern __shared__ __align__(16) uint64_t smem32[];
   const int lane = threadIdx.x & 31;
@@ -445,7 +452,7 @@ __global__ void __launch_bounds__(kOps32Threads, 3)
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t nchunks = static_cast<uint32_t>((n + 31) >> 5);
   const uint32_t stash_n = v.ctrl->stash_n;
-  Stage32 sg = stage32_init(smem32, threadIdx.x >> 5, lane);
+  Stage32 sg = stage32_init(smem32, threadIdx.x >> 5, lane, stage32_words(MODE));
   Counters32 cnt;
   for (uint32_t c = warp0; c < nchunks; c += nwarps)
     run_chunk32<MODE, LAYOUT>(v, stash_n, a, c, n, ovf, cnt, sg, lane);
@@ -705,63 +712,71 @@ __global__ void __launch_bounds__(kMaint32Threads) k32_maint(View32 v) {
   }
 }
 
+// Resident blocks per SM of each bulk kernel, per layout and mode (set once
+// per process by setup32; every GPU of the machine is the same model).
+int g_occ32[2][4] = {{1, 1, 1, 1}, {1, 1, 1, 1}};
+
 template <int MODE, int LAYOUT>
 cudaError_t launch32_t(const View32& v, const Ops32& a, uint64_t n, const List32& ovf,
-                       int blocks_cap, cudaStream_t s) {
+                       int num_sms, cudaStream_t s) {
   const uint64_t chunks = (n + 31) / 32;
   uint64_t blocks = (chunks + (kOps32Threads / 32) - 1) / (kOps32Threads / 32);
-  if (blocks > static_cast<uint64_t>(blocks_cap)) blocks = blocks_cap;
+  const uint64_t cap = static_cast<uint64_t>(num_sms) * g_occ32[LAYOUT][MODE];
+  if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
-  k32_ops<MODE, LAYOUT><<<static_cast<unsigned>(blocks), kOps32Threads, kStage32Smem, s>>>(v, a, n,
-                                                                                         ovf);
+  k32_ops<MODE, LAYOUT><<<static_cast<unsigned>(blocks), kOps32Threads, stage32_smem(MODE), s>>>(
+      v, a, n, ovf);
   return cudaGetLastError();
 }
 
 template <int LAYOUT>
 cudaError_t launch32_l(int mode, const View32& v, const Ops32& a, uint64_t n, const List32& ovf,
-                       int blocks_cap, cudaStream_t s) {
+                       int num_sms, cudaStream_t s) {
   switch (mode) {
     case kModeFind:
-      return launch32_t<kModeFind, LAYOUT>(v, a, n, ovf, blocks_cap, s);
+      return launch32_t<kModeFind, LAYOUT>(v, a, n, ovf, num_sms, s);
     case kModeInsert:
-      return launch32_t<kModeInsert, LAYOUT>(v, a, n, ovf, blocks_cap, s);
+      return launch32_t<kModeInsert, LAYOUT>(v, a, n, ovf, num_sms, s);
     case kModeErase:
-      return launch32_t<kModeErase, LAYOUT>(v, a, n, ovf, blocks_cap, s);
+      return launch32_t<kModeErase, LAYOUT>(v, a, n, ovf, num_sms, s);
     default:
-      return launch32_t<kModeMixed, LAYOUT>(v, a, n, ovf, blocks_cap, s);
+      return launch32_t<kModeMixed, LAYOUT>(v, a, n, ovf, num_sms, s);
   }
+}
+
+template <int MODE, int LAYOUT>
+cudaError_t setup32_mode() {
+  const int smem = static_cast<int>(stage32_smem(MODE));
+  cudaError_t e = cudaFuncSetAttribute(k32_ops<MODE, LAYOUT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int b = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k32_ops<MODE, LAYOUT>, kOps32Threads,
+                                                      stage32_smem(MODE));
+  g_occ32[LAYOUT][MODE] = b > 0 ? b : 1;
+  return e;
 }
 
 template <int LAYOUT>
 cudaError_t setup32_l(int* blocks_per_sm) {
-  const int smem = static_cast<int>(kStage32Smem);
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k32_ops<kModeFind, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k32_ops<kModeInsert, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k32_ops<kModeErase, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k32_ops<kModeMixed, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = setup32_mode<kModeFind, LAYOUT>();
+  if (e == cudaSuccess) e = setup32_mode<kModeInsert, LAYOUT>();
+  if (e == cudaSuccess) e = setup32_mode<kModeErase, LAYOUT>();
+  if (e == cudaSuccess) e = setup32_mode<kModeMixed, LAYOUT>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k32_maint<LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kMaint32SmemWords * 4));
-  int b = 0;
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k32_ops<kModeInsert, LAYOUT>,
-                                                      kOps32Threads, kStage32Smem);
-  *blocks_per_sm = b > 0 ? b : 1;
+  *blocks_per_sm = g_occ32[LAYOUT][kModeInsert];
   return e;
 }
 
 }  // namespace
 
 cudaError_t launch32_ops(int mode, const View32& v, const Ops32& a, uint64_t n, const List32& ovf,
-                         int blocks_cap, cudaStream_t s) {
+                         int num_sms, cudaStream_t s) {
   return v.layout == HIVE32_KEY_ONLY
-             ? launch32_l<HIVE32_KEY_ONLY>(mode, v, a, n, ovf, blocks_cap, s)
-             : launch32_l<HIVE32_KEY16_VAL16>(mode, v, a, n, ovf, blocks_cap, s);
+             ? launch32_l<HIVE32_KEY_ONLY>(mode, v, a, n, ovf, num_sms, s)
+             : launch32_l<HIVE32_KEY16_VAL16>(mode, v, a, n, ovf, num_sms, s);
 }
 
 cudaError_t launch32_overflow(const View32& v, const List32& in, uint8_t* status, int blocks,

@@ -478,6 +478,7 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
     const int cap = static_cast<int>(cfg->blocks_per_sm);
     t->L.ops_blocks_per_sm = std::min(t->L.ops_blocks_per_sm, cap);
     t->L.staged_blocks_per_sm = std::min(t->L.staged_blocks_per_sm, cap);
+    t->L.staged1_blocks_per_sm = std::min(t->L.staged1_blocks_per_sm, cap);
   }
   if (e == cudaSuccess && cfg->resizable && cfg->map_on_demand) {
     // reserve the address range of nb_max buckets, back only nb_init of them

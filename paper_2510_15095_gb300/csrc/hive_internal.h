@@ -121,7 +121,8 @@ enum OpMode : int { kModeFind = 0, kModeInsert = 1, kModeErase = 2, kModeMixed =
 struct Launch {
   int num_sms;
   int ops_blocks_per_sm;     // bulk kernel, fragments loaded from global memory
-  int staged_blocks_per_sm;  // bulk kernel, probes staged in shared memory
+  int staged_blocks_per_sm;  // bulk kernel, paired insert rounds staged in shared memory
+  int staged1_blocks_per_sm; // bulk kernel, single-bucket rounds staged in shared memory
   int fused_blocks_per_sm;   // single-kernel mixed batch
   int ovf_blocks_per_sm;
   int multi_blocks_per_sm;
@@ -181,7 +182,7 @@ struct List32 {
   unsigned int* count;
 };
 cudaError_t launch32_ops(int mode, const View32& v, const Ops32& a, uint64_t n, const List32& ovf,
-                         int blocks_cap, cudaStream_t s);
+                         int num_sms, cudaStream_t s);
 cudaError_t launch32_overflow(const View32& v, const List32& in, uint8_t* status, int blocks,
                               cudaStream_t s);
 cudaError_t launch32_maint(const View32& v, cudaStream_t s);

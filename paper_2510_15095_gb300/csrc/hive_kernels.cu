@@ -63,6 +63,9 @@ constexpr int kOpsThreads = 256;
 #ifndef HIVE_STAGE_LSU_S32
 #define HIVE_STAGE_LSU_S32 0
 #endif
+#ifndef HIVE_STAGED_SMALL_MIN_BLOCKS
+#define HIVE_STAGED_SMALL_MIN_BLOCKS 4  // 32 KB of staging per block (S = 16 single rounds)
+#endif
 #ifndef HIVE_STAGED_MIN_BLOCKS
 #define HIVE_STAGED_MIN_BLOCKS 3  // 64 KB of staging per block: three blocks fit an SM
 #endif
@@ -239,6 +242,19 @@ constexpr int kStageBytesPerWarp = 8 * (kStageWords + 2);
 constexpr uint32_t kMbarSpinLimit = 1u << 22;
 constexpr size_t kStageSmemBytes = static_cast<size_t>(kOpsThreads / 32) * kStageBytesPerWarp;
 
+// Staging words a warp of mode MODE needs: a paired insert round fills the
+// whole 8 KB; a single-bucket round holds 32 buckets (4 KB at S = 16), which
+// lets four 256-thread blocks share an SM.
+__host__ __device__ constexpr int stage_words(int mode, int S) {
+  return mode == kModeInsert ? kStageWords : 32 * S;
+}
+__host__ __device__ constexpr size_t stage_smem(int mode, int S) {
+  return static_cast<size_t>(kOpsThreads / 32) * 8u * (stage_words(mode, S) + 2);
+}
+__host__ __device__ constexpr int staged_min_blocks(int mode, int S) {
+  return stage_words(mode, S) < kStageWords ? HIVE_STAGED_SMALL_MIN_BLOCKS : HIVE_STAGED_MIN_BLOCKS;
+}
+
 struct Stage {
   uint64_t* bar;   // mbarrier
   uint64_t* buf;   // kStageWords words, 16-byte aligned
@@ -246,10 +262,12 @@ struct Stage {
   bool dead;       // a wait gave up: copies may still land, the buffer is not reused
 };
 
-// Sets up the calling warp's stage in the kernel's dynamic shared memory.
-__device__ __forceinline__ Stage stage_init(uint64_t* smem, int warp_in_block, int lane) {
+// Sets up the calling warp's stage in the kernel's dynamic shared memory
+// (`words` staging words per warp after its barrier).
+__device__ __forceinline__ Stage stage_init(uint64_t* smem, int warp_in_block, int lane,
+                                            int words = kStageWords) {
   Stage sg;
-  uint64_t* base = smem + static_cast<size_t>(warp_in_block) * (kStageBytesPerWarp / 8);
+  uint64_t* base = smem + static_cast<size_t>(warp_in_block) * (words + 2);
   sg.bar = base;
   sg.buf = base + 2;
   sg.phase = 0;
@@ -940,7 +958,7 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
 
 template <int MODE, int S>
 __global__ void __launch_bounds__(kOpsThreads, staged_mode(MODE, S)
-                                                   ? HIVE_STAGED_MIN_BLOCKS
+                                                   ? staged_min_blocks(MODE, S)
                                                    : HIVE_OPS_MIN_BLOCKS)
     k_ops(View v, OpPtrs a, uint64_t n, List ovf) {
   const int lane = threadIdx.x & 31;
@@ -953,7 +971,7 @@ __global__ void __launch_bounds__(kOpsThreads, staged_mode(MODE, S)
   if (staged_mode(MODE, S)) {
     // bucket reads staged in shared memory by bulk copies
     extern __shared__ __align__(16) uint64_t ops_smem[];
-    Stage sg = stage_init(ops_smem, threadIdx.x >> 5, lane);
+    Stage sg = stage_init(ops_smem, threadIdx.x >> 5, lane, stage_words(MODE, S));
     // inputs are loaded one chunk ahead, so their latency hides behind the
     // current chunk's probes and claims
     OpIn nxt{};
@@ -1891,12 +1909,13 @@ cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys
   const uint64_t warps_per_block = kOpsThreads / 32;
   uint64_t blocks = (chunks + warps_per_block - 1) / warps_per_block;
   constexpr bool kStaged = staged_mode(MODE, S);
-  const int per_sm = kStaged ? L.staged_blocks_per_sm : L.ops_blocks_per_sm;
+  const int per_sm = !kStaged ? L.ops_blocks_per_sm
+                     : (MODE == kModeInsert ? L.staged_blocks_per_sm : L.staged1_blocks_per_sm);
   const uint64_t cap = static_cast<uint64_t>(L.num_sms) * per_sm;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   const OpPtrs a{ops, keys, vals, vals_out, found, status};
-  const size_t smem = kStaged ? kStageSmemBytes : 0;
+  const size_t smem = kStaged ? stage_smem(MODE, S) : 0;
   k_ops<MODE, S><<<static_cast<unsigned>(blocks), kOpsThreads, smem, s>>>(v, a, n, ovf);
   return cudaGetLastError();
 }
@@ -2067,19 +2086,26 @@ cudaError_t occupancy_s(Launch* L) {
                                                                 kOpsThreads, 0);
   if (e != cudaSuccess) return e;
   L->ops_blocks_per_sm = b > 0 ? b : 1;
-  const int stage_smem = static_cast<int>(kStageSmemBytes);
-  e = cudaFuncSetAttribute(k_ops<kModeFind, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage_smem);
+  e = cudaFuncSetAttribute(k_ops<kModeFind, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(stage_smem(kModeFind, S)));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ops<kModeInsert, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage_smem);
+    e = cudaFuncSetAttribute(k_ops<kModeInsert, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(stage_smem(kModeInsert, S)));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ops<kModeErase, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage_smem);
+    e = cudaFuncSetAttribute(k_ops<kModeErase, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(stage_smem(kModeErase, S)));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ops<kModeMixed, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage_smem);
+    e = cudaFuncSetAttribute(k_ops<kModeMixed, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(stage_smem(kModeMixed, S)));
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeInsert, S>, kOpsThreads,
-                                                    kStageSmemBytes);
+                                                    stage_smem(kModeInsert, S));
   if (e != cudaSuccess) return e;
   L->staged_blocks_per_sm = b > 0 ? b : 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeMixed, S>, kOpsThreads,
+                                                    stage_smem(kModeMixed, S));
+  if (e != cudaSuccess) return e;
+  L->staged1_blocks_per_sm = b > 0 ? b : 1;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused<S>, kOpsThreads, 0);
   if (e != cudaSuccess) return e;
   L->fused_blocks_per_sm = b > 0 ? b : 1;
