@@ -59,3 +59,28 @@ def test_host_validation_without_gpu(lib):
     bad.shrink_num, bad.shrink_den = 9, 10
     assert lib.hive_create(C.byref(bad), None, C.byref(h)) == 1
     assert lib.hive_destroy(None) == 0
+
+
+def test_host_validation_of_later_entry_points(lib):
+    """Argument checks of the single-kernel batch, the on-demand mapping flag
+    and the 32-bit-entry tables, all before any CUDA call."""
+    from paper_2510_15095_gb300 import hive
+    assert lib.hive_execute_fused(None, None, None, None, 4, None, None, None) == 1
+    cfg = hive.Config()
+    lib.hive_config_default(C.byref(cfg))
+    assert cfg.map_on_demand == 0
+    cfg.resizable = 1
+    cfg.map_on_demand = 2
+    h = C.c_void_p()
+    assert lib.hive_create(C.byref(cfg), None, C.byref(h)) == 1
+    c32 = hive.Config32()
+    lib.hive32_config_default(C.byref(c32))
+    assert c32.layout == hive.KEY16_VAL16 and c32.max_evictions == 16
+    for field, bad in (("layout", 7), ("slots", 16), ("max_evictions", 0), ("lock_spin_limit", 0)):
+        b = hive.Config32()
+        lib.hive32_config_default(C.byref(b))
+        setattr(b, field, bad)
+        assert lib.hive32_create(C.byref(b), None, C.byref(h)) == 1, field
+    assert lib.hive32_insert(None, None, None, 3, None, None) == 1
+    assert lib.hive32_find(None, None, 3, None, None, None) == 1
+    assert lib.hive32_destroy(None) == 0
