@@ -238,9 +238,7 @@ struct Geo {
 // kMbarSpinLimit tries raises the table's sticky TIMEOUT error, marks the
 // stage dead and redoes the round from global memory.
 constexpr int kStageWords = 1024;
-constexpr int kStageBytesPerWarp = 8 * (kStageWords + 2);
 constexpr uint32_t kMbarSpinLimit = 1u << 22;
-constexpr size_t kStageSmemBytes = static_cast<size_t>(kOpsThreads / 32) * kStageBytesPerWarp;
 
 // Staging words a warp of mode MODE needs: a paired insert round fills the
 // whole 8 KB; a single-bucket round holds 32 buckets (4 KB at S = 16), which
@@ -1019,8 +1017,9 @@ struct OvfCounters {
   Ctrl* reserved_in = nullptr;  // control block of the table the reservation belongs to
 };
 
-__device__ __forceinline__ void flush_ovf_counters(const View& v, OvfCounters& oc, int lane) {
-  if (lane == 0) {
+// `lead`: the calling lane leads its group and holds the group's counters.
+__device__ __forceinline__ void flush_ovf_counters(const View& v, OvfCounters& oc, bool lead) {
+  if (lead) {
     Ctrl* c = v.ctrl;
     if (oc.added) atomicAdd(&c->size, static_cast<unsigned long long>(oc.added));
     if (oc.claim) atomicAdd(&c->stats[kStClaimedSlow], static_cast<unsigned long long>(oc.claim));
@@ -1039,8 +1038,8 @@ __device__ __forceinline__ void flush_ovf_counters(const View& v, OvfCounters& o
 }
 
 // Gives back a warp's unused stash reservation.
-__device__ __forceinline__ void release_reservation(OvfCounters& oc, int lane) {
-  if (lane == 0 && oc.reserved_in) atomicSub(&oc.reserved_in->stash_claims, 1u);
+__device__ __forceinline__ void release_reservation(OvfCounters& oc, bool lead) {
+  if (lead && oc.reserved_in) atomicSub(&oc.reserved_in->stash_claims, 1u);
   oc.reserved_in = nullptr;
 }
 
@@ -1052,6 +1051,14 @@ template <int S>
 __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uint32_t idx,
                                               uint32_t seg, uint8_t* status, int resizable,
                                               const List& pend, OvfCounters& oc, int lane) {
+  // The item belongs to a group of S lanes (a half-warp at S = 16, so a warp
+  // carries two chains at once): group lane gl holds slot gl of the bucket in
+  // hand, and group lane 0 leads.
+  constexpr unsigned kGroupBits = (S >= 32) ? 0xFFFFFFFFu : ((1u << S) - 1u);
+  const int gl = lane & (S - 1);
+  const int gb = lane - gl;
+  const unsigned gmask = kGroupBits << gb;
+  auto group_ballot = [&](bool pred) { return (__ballot_sync(gmask, pred) >> gb) & kGroupBits; };
   const uint32_t key0 = key_of(word0);
   const uint32_t b1 = lh_bucket(bithash1(key0), v.M, v.p);
   const uint32_t b2 = lh_bucket(bithash2(key0), v.M, v.p);
@@ -1060,9 +1067,8 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
   int outcome = 0;
   // the BitHash1 bucket, read now for the first eviction round: most items
   // here find both buckets still full
-  const uint64_t w0 =
-      lane < S ? ld_relaxed64(v.buckets + static_cast<uint64_t>(b1) * S + lane) : kEmptyWord;
-  if (lane == 0) {
+  const uint64_t w0 = ld_relaxed64(v.buckets + static_cast<uint64_t>(b1) * S + gl);
+  if (gl == 0) {
     // both free masks in one round trip; claim where a bit is free
     const uint32_t m1 = ld_relaxed32(v.masks + b1);
     const uint32_t m2 = ld_relaxed32(v.masks + b2);
@@ -1077,7 +1083,7 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
       if (!oc.reserved_in) outcome = 3;
     }
   }
-  outcome = __shfl_sync(kFull, outcome, 0);
+  outcome = __shfl_sync(gmask, outcome, 0, S);
 
   if (outcome == 0) {
     uint64_t cur = word0;
@@ -1086,9 +1092,7 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
     for (uint32_t r = 0; r < v.max_evictions; ++r) {
       // Look ahead: each lane checks whether the word in its slot could move
       // to its other candidate bucket without a further eviction.
-      const uint64_t w = r == 0 ? w0
-                                : (lane < S ? ld_relaxed64(v.buckets + static_cast<uint64_t>(b) * S + lane)
-                                            : kEmptyWord);
+      const uint64_t w = r == 0 ? w0 : ld_relaxed64(v.buckets + static_cast<uint64_t>(b) * S + gl);
       uint32_t am = 0;  // free mask of this word's other candidate bucket
       if (w != kEmptyWord) {
         const uint32_t k = key_of(w);
@@ -1097,9 +1101,9 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
         const uint32_t alt = (a1 == b) ? a2 : a1;
         if (alt != b) am = ld_relaxed32(v.masks + alt);
       }
-      const unsigned gm = __ballot_sync(kFull, am != 0u);
-      const unsigned occ = __ballot_sync(kFull, lane < S && w != kEmptyWord);
-      const bool has_empty = __ballot_sync(kFull, lane < S && w == kEmptyWord) != 0u;
+      const unsigned gm = group_ballot(am != 0u);
+      const unsigned occ = group_ballot(w != kEmptyWord);
+      const bool has_empty = occ != kGroupBits;
       int res = 0;  // 0: evicted `victim`, 1: placed, 2: lock wait gave up, 3: redo the round
       uint64_t victim = kEmptyWord;
       // victim: an occupied slot whose word can move on at once, else an
@@ -1109,11 +1113,12 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
         vs = __ffs(gm) - 1;
       } else if (occ) {
         const uint32_t start = (bithash2(key_of(cur)) + r) & (S - 1);
-        const unsigned rot = (occ >> start) | (start ? (occ << (32 - start)) : 0u);
-        vs = (start + __ffs(rot) - 1) & 31;
+        const unsigned rot =
+            start ? (((occ >> start) | (occ << (S - start))) & kGroupBits) : occ;
+        vs = (start + __ffs(rot) - 1) & (S - 1);
       }
-      const uint32_t vmask = __shfl_sync(kFull, am, vs & 31);
-      if (lane == 0) {
+      const uint32_t vmask = __shfl_sync(gmask, am, vs & (S - 1), S);
+      if (gl == 0) {
         ++oc.rounds;
         if (!lock_bucket(v, b)) {
           res = 2;
@@ -1131,8 +1136,8 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
           unlock_bucket(v, b);
         }
       }
-      res = __shfl_sync(kFull, res, 0);
-      victim = __shfl_sync(kFull, victim, 0);
+      res = __shfl_sync(gmask, res, 0, S);
+      victim = __shfl_sync(gmask, victim, 0, S);
       if (res == 1) {
         placed = true;
         break;
@@ -1148,16 +1153,16 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
       if (nb == b) break;  // both candidates are this bucket: no alternative
       b = nb;
       int ok = 0;
-      if (lane == 0) ok = claim_pub<S>(v, b, cur, vmask);
-      if (__shfl_sync(kFull, ok, 0)) {
+      if (gl == 0) ok = claim_pub<S>(v, b, cur, vmask);
+      if (__shfl_sync(gmask, ok, 0, S)) {
         placed = true;
         break;
       }
     }
-    if (lane == 0) {
+    if (gl == 0) {
       if (placed && oc.reserved_in && ld_relaxed32(&v.ctrl->stash_claims) >= v.stash_cap) {
         // every free stash word is reserved: give this one back so that a
-        // waiting warp can go on
+        // waiting group can go on
         atomicSub(&v.ctrl->stash_claims, 1u);
         oc.reserved_in = nullptr;
       }
@@ -1171,7 +1176,7 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
     outcome = placed ? 1 : 2;
   }
 
-  if (lane == 0) {
+  if (gl == 0) {
     if (outcome == 3) {
       ++oc.pend;
       if (resizable) {
@@ -1193,15 +1198,17 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
 template <int S>
 __global__ void __launch_bounds__(kOvfThreads)
     k_overflow(View v, List in, List pend, int resizable, uint8_t* __restrict__ status) {
+  // one item per group of S lanes at a time
   const int lane = threadIdx.x & 31;
-  const unsigned warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  const unsigned group0 = (blockIdx.x * blockDim.x + threadIdx.x) / S;
+  const unsigned ngroups = (gridDim.x * blockDim.x) / S;
+  const bool lead = (lane & (S - 1)) == 0;
   const unsigned total = *in.count;
   OvfCounters oc;
-  for (unsigned it = warp0; it < total; it += nwarps)
+  for (unsigned it = group0; it < total; it += ngroups)
     overflow_item<S>(v, in.words[it], in.idx[it], 0, status, resizable, pend, oc, lane);
-  release_reservation(oc, lane);
-  flush_ovf_counters(v, oc, lane);
+  release_reservation(oc, lead);
+  flush_ovf_counters(v, oc, lead);
 }
 
 // ----------------------------------------------------------------------------
@@ -1552,8 +1559,8 @@ __global__ void __launch_bounds__(kOpsThreads, 3)
   unsigned retries = 0;
   for (uint32_t c = warp0; c < nchunks; c += nwarps)
     run_chunk_fused<S>(v, stash_n, a, c, n, pend, resizable, cnt, oc, retries, lane);
-  release_reservation(oc, lane);
-  flush_ovf_counters(v, oc, lane);
+  release_reservation(oc, lane == 0);
+  flush_ovf_counters(v, oc, lane == 0);
   flush_counters(v, cnt, lane);
   if (lane == 0 && retries)
     atomicAdd(&v.ctrl->stats[kStFusedRetries], static_cast<unsigned long long>(retries));
@@ -1834,19 +1841,21 @@ __global__ void __launch_bounds__(kOpsThreads, HIVE_MULTI_MIN_BLOCKS)
 template <int S>
 __global__ void __launch_bounds__(kOvfThreads)
     k_multi_overflow(const MultiSeg* __restrict__ segs, const View* __restrict__ views, List in) {
+  // one item per group of S lanes at a time
   const int lane = threadIdx.x & 31;
-  const unsigned warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  const unsigned group0 = (blockIdx.x * blockDim.x + threadIdx.x) / S;
+  const unsigned ngroups = (gridDim.x * blockDim.x) / S;
+  const bool lead = (lane & (S - 1)) == 0;
   const unsigned total = *in.count;
   const List none{nullptr, nullptr, nullptr, nullptr};
   OvfCounters oc;
-  for (unsigned it = warp0; it < total; it += nwarps) {
+  for (unsigned it = group0; it < total; it += ngroups) {
     const uint32_t sg = in.seg[it];
     const View v = views[segs[sg].table];
     overflow_item<S>(v, in.words[it], in.idx[it], sg, segs[sg].status, 0, none, oc, lane);
-    flush_ovf_counters(v, oc, lane);
+    flush_ovf_counters(v, oc, lead);
   }
-  release_reservation(oc, lane);
+  release_reservation(oc, lead);
 }
 
 // One CTA per table of the batch: stash maintenance (exits at once when
