@@ -4,10 +4,11 @@
 //
 // Same algorithm as the 64-bit table, fixed capacity:
 //   k32_ops<MODE, LAYOUT>  bulk find / insert (steps 1-2) / erase / mixed.
-//                          Every probe round is staged: each lane bulk-copies
-//                          its op's bucket(s) into its warp's shared-memory
-//                          buffer (cp.async.bulk + mbarrier) and scans them
-//                          itself, 16 bytes (four slots) per read.
+//                          Every probe round is staged: the op buckets are
+//                          copied into the warp's shared-memory buffer
+//                          (16-byte cp.async, eight lanes per bucket) and each
+//                          lane scans its op's bucket(s) itself, 16 bytes (four
+//                          slots) per read.
 //   k32_overflow<LAYOUT>   steps 3-4: bounded cuckoo eviction under the
 //                          bucket lock, warp per item (one slot per lane),
 //                          then the stash.

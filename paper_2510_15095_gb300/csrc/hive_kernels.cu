@@ -41,7 +41,7 @@ constexpr int kOpsThreads = 256;
 #define HIVE_MULTI_MIN_BLOCKS 3  // the multi-table bulk kernel also holds a table view per warp
 #endif
 // Bulk-kernel modes (bit kModeFind, kModeInsert, ...) whose probes are staged
-// in shared memory by bulk copies, per bucket width; the others load
+// in shared memory, per bucket width; the others load
 // fragments straight from global memory with the warp-wide match-and-elect.
 // Measured on the 2^26-slot, 95%-load bench workload, staging wins for
 // every mode at both widths (with the copy path chosen below per width).
@@ -225,16 +225,17 @@ struct Geo {
   static constexpr unsigned LM = (L >= 32) ? 0xFFFFFFFFu : ((1u << L) - 1u);
 };
 
-// ---- Shared-memory staging of bucket reads (TMA bulk copies) ----
+// ---- Shared-memory staging of bucket reads ----
 //
-// A kernel that stages its probes gives each warp one mbarrier and a buffer of
-// kStageWords words (8 KB): every bucket a probe round needs -- the 32 ops'
+// A kernel that stages its probes gives each warp one mbarrier and a buffer
+// (stage_words() below): every bucket a probe round needs -- the 32 ops'
 // buckets of a single-bucket round, or both candidate buckets of 32 (S = 16)
-// or 16 (S = 32) ops of a paired round -- is requested with one whole-bucket
-// cp.async.bulk per bucket, so the warp has all of them in flight at once
-// without holding registers, and the barrier counts the arriving bytes.  The
-// evaluation then reads 16-byte fragments out of shared memory in the same
-// order the global-memory probe reads them.  A wait that does not end within
+// or 16 (S = 32) ops of a paired round -- is copied in before any compare, so
+// the warp has all of them in flight at once without holding registers.
+// 128-byte buckets are copied with 16-byte cp.async through the load/store
+// path (stage_issue_lsu); 256-byte buckets with one bulk copy (TMA) each,
+// counted by the barrier (stage_issue).  Each lane then scans its own op's
+// buckets in shared memory.  A barrier wait that does not end within
 // kMbarSpinLimit tries raises the table's sticky TIMEOUT error, marks the
 // stage dead and redoes the round from global memory.
 constexpr int kStageWords = 1024;
@@ -697,7 +698,7 @@ __device__ __forceinline__ void probe_round(const View& v, unsigned need, uint32
 // so that the eight lanes of a shared-memory wavefront read eight different
 // bank groups, and one compare per slot against the op's key (a key sits in
 // at most one slot of the table).  Free counts and first free slots come from
-// the free masks, read from global memory while the bulk copies are in flight:
+// the free masks, read from global memory while the copies are in flight:
 // they only steer the claim, whose fetch_and result is the authority.  This
 // takes a few instructions per slot where the warp-wide match-and-elect takes
 // several ballots per 16-byte fragment, and the staged kernel is bound by
@@ -752,7 +753,7 @@ __device__ __forceinline__ void probe_pair_round(const View& v, unsigned need, u
   constexpr int BO = kStageWords / (2 * S);
   constexpr unsigned BM = (BO >= 32) ? 0xFFFFFFFFu : ((1u << BO) - 1u);
   if (sg) {
-    // free masks of both buckets, in flight beside the bulk copies
+    // free masks of both buckets, in flight beside the copies
     const bool mine = (need >> lane) & 1u;
     const uint32_t m1 = mine ? ld_relaxed32(v.masks + b1) : 0u;
     const uint32_t m2 = mine ? ld_relaxed32(v.masks + b2) : 0u;
@@ -967,7 +968,7 @@ __global__ void __launch_bounds__(kOpsThreads, staged_mode(MODE, S)
   const uint32_t stash_n = v.ctrl->stash_n;
   LaneCounters cnt;
   if (staged_mode(MODE, S)) {
-    // bucket reads staged in shared memory by bulk copies
+    // bucket reads staged in shared memory
     extern __shared__ __align__(16) uint64_t ops_smem[];
     Stage sg = stage_init(ops_smem, threadIdx.x >> 5, lane, stage_words(MODE, S));
     // inputs are loaded one chunk ahead, so their latency hides behind the
