@@ -246,15 +246,20 @@ def test_resizable_bulk_insert_erase(H):
     t.close()
 
 
-def test_2e26_slots_95pct_load(H):
+@pytest.mark.parametrize("bs", [16])
+def test_2e26_slots_95pct_load(H, bs):
     """The load-factor sweep table at full size: 2^26 slots filled to 95%
-    (63,753,421 keys) in one launch, then 2^26 finds at 50% hit rate in the
-    bench's launch configuration.  Every find is checked against the property
-    that holds at any size (hit -> the key's value, miss -> not found); a 2^21
-    sample is checked against the oracle; the dump passes the invariants."""
+    (63,753,421 keys) in one launch, then 2^26 finds at 50% hit rate and the
+    2^24-op mixed batch (1:2:1 at 95%), in the bench's launch configuration
+    (16-slot buckets, the bench's tuned width; 32-slot buckets are covered at
+    smaller sizes above).  Every result is checked
+    against the properties that hold at any size (hit -> the key's value,
+    miss -> not found, new insert -> INSERTED, erase of a live key -> ERASED);
+    a 2^21 sample of the finds is checked against the oracle; the dump passes
+    the invariants."""
     slots = 1 << 26
     w = W.fill_and_query(seed=2, slots=slots, load_num=19, load_den=20, n_find=1 << 26)
-    t = H.HiveTable(slots)
+    t = H.HiveTable(slots, bucket_slots=bs)
     st = t.insert(up(H, w["insert_keys"]), up(H, w["insert_vals"])).cpu().numpy()
     assert (st == H.INSERTED).all()
     assert t.size() == w["insert_keys"].size
@@ -270,6 +275,19 @@ def test_2e26_slots_95pct_load(H):
     sample = rng.integers(0, w["find_keys"].size, 1 << 21)
     ev, ef = d.find(w["find_keys"][sample])
     assert np.array_equal(gv[sample], ev) and np.array_equal(gf[sample].astype(np.uint8), ef)
+    # the mixed batch: new inserts, erases of live keys, finds of other live keys
+    n_mix = 1 << 24
+    new, _ = W.take_keys(2, 1 << 31, n_mix // 4)
+    ops, keys, vals = W.mixed_batch(rng, w["insert_keys"], new, n_mix // 4, n_mix // 4,
+                                    n_mix // 2, seed=2)
+    vo, ms = t.execute(torch.from_numpy(ops).cuda(), up(H, keys), up(H, vals))
+    vo, ms = H.to_host_u32(vo), ms.cpu().numpy()
+    ins, era, fnd = ops == 0, ops == 2, ops == 1
+    assert (ms[ins] == H.INSERTED).all() and (ms[era] == H.ERASED).all()
+    assert (ms[fnd] == H.FOUND).all()
+    assert np.array_equal(vo[fnd], W.values_for(keys[fnd], 2))
+    d.execute(ops, keys, vals)
+    assert t.size() == len(d)
     check_image(t, d)
     assert t.check() == 0
     t.close()
