@@ -40,3 +40,39 @@ def test_converges_to_uniform(which, kind):
                 else rng.choice(1 << 32, n, replace=False).astype(np.uint32))
         c = csr(which, keys)
         assert abs(c - 1.0) < 0.01, (which, kind, n, c)
+
+
+def _fill_overflow(hashes, n_buckets, slots, n_keys):
+    """Greedy balanced placement (the bucket with the most free slots, ties
+    to the earlier hash) of n_keys keys; returns the fraction of keys whose
+    candidate buckets were all full (the ones that would need eviction)."""
+    load = np.zeros(n_buckets, np.int64)
+    cand = np.stack([h % n_buckets for h in hashes], axis=1)
+    over = 0
+    for row in cand[:n_keys]:
+        free = slots - load[row]
+        j = int(np.argmax(free))
+        if free[j] <= 0:
+            over += 1
+            continue
+        load[row[j]] += 1
+    return over / n_keys
+
+
+def test_three_choices_cut_overflow_but_two_suffice():
+    """Section V (hash functions): a third hash function improves the spread
+    of keys only marginally.  With balanced two-choice placement of 16-slot
+    buckets filled to 95%, few keys find both buckets full; a third choice
+    (here a Fibonacci multiply-shift of our own, since the paper's third
+    function is third-party code) removes most of those, at the price of one
+    more bucket probe for every lookup."""
+    n_buckets, slots = 1 << 12, 16
+    n = n_buckets * slots * 95 // 100
+    keys = np.arange(1, n + 1, dtype=np.uint32) * np.uint32(2654435761)
+    h1 = oracle.bithash_many(1, keys).astype(np.int64)
+    h2 = oracle.bithash_many(2, keys).astype(np.int64)
+    h3 = ((keys.astype(np.uint64) * np.uint64(0x9E3779B97F4A7C15)) >> np.uint64(32)).astype(np.int64)
+    two = _fill_overflow([h1, h2], n_buckets, slots, n)
+    three = _fill_overflow([h1, h2, h3], n_buckets, slots, n)
+    assert two < 0.02          # two choices already place more than 98% at 95% load
+    assert three < two / 2     # a third choice removes most of the rest
