@@ -196,7 +196,8 @@ hive_status hive_erase(hive_table* t, const uint32_t* keys, uint64_t n, uint8_t*
                        void* stream);
 
 /* Mixed batch (Section V-C2, imbalanced workloads).  ops[n] holds HIVE_OP_*.
- * vals (nullable unless the batch holds inserts) supplies insert values.
+ * vals[n] supplies insert values; it may be NULL, and the batch's inserts
+ * then store value 0 (the kernels never read a NULL vals).
  * vals_out[n] (nullable): find results, 0 otherwise.  status[n] (nullable):
  * per-op code (finds report FOUND / NOT_FOUND). */
 hive_status hive_execute(hive_table* t, const uint8_t* ops, const uint32_t* keys,
@@ -411,7 +412,8 @@ hive_status hive32_find(hive32_table* t, const uint32_t* keys, uint64_t n, uint3
 /* Delete: status nullable, ERASED / NOT_FOUND / RESERVED_KEY. */
 hive_status hive32_erase(hive32_table* t, const uint32_t* keys, uint64_t n, uint8_t* status,
                          void* stream);
-/* Mixed batch of HIVE_OP_* codes, as hive_execute. */
+/* Mixed batch of HIVE_OP_* codes, as hive_execute (a NULL vals makes the
+ * batch's inserts store value 0). */
 hive_status hive32_execute(hive32_table* t, const uint8_t* ops, const uint32_t* keys,
                            const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* status,
                            void* stream);
