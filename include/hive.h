@@ -381,7 +381,7 @@ typedef struct {
   uint64_t slots;           /* capacity in slots, rounded up to a multiple of 32 (>= 32) */
   uint32_t layout;          /* HIVE32_KEY16_VAL16 or HIVE32_KEY_ONLY */
   uint32_t max_evictions;   /* cuckoo displacement bound per insert (1..64, default 16) */
-  uint32_t stash_permille;  /* stash capacity in 1/1000 of the slots (default 10; at least 1024) */
+  uint32_t stash_permille;  /* stash capacity in 1/1000 of the slots (default 10, at most 1000; at least 1024 entries) */
   uint32_t lock_spin_limit; /* bounded bucket-lock wait, in tries (default 1 << 16) */
 } hive32_config;
 

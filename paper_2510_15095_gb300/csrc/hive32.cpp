@@ -165,24 +165,26 @@ hive_status hive32_create(const hive32_config* cfg, void* stream, hive32_table**
   if (cfg->max_evictions < 1 || cfg->max_evictions > 64)
     return fail32(HIVE_ERR_INVALID_ARG, "max_evictions must be in 1..64");
   if (cfg->lock_spin_limit == 0) return fail32(HIVE_ERR_INVALID_ARG, "lock_spin_limit must be > 0");
+  if (cfg->stash_permille > 1000) return fail32(HIVE_ERR_INVALID_ARG, "stash_permille must be <= 1000");
   const uint64_t nb = (cfg->slots + kS - 1) / kS;
   if (nb > kMaxBuckets32) return fail32(HIVE_ERR_INVALID_ARG, "too many slots");
   hive32_table* t = new (std::nothrow) hive32_table();
   if (!t) return fail32(HIVE_ERR_OOM, "host allocation failed");
   t->cfg = *cfg;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaGetDevice(&t->device);
   t->nb = nb;
   uint64_t pow2 = 1;
   while (pow2 * 2 <= nb) pow2 *= 2;
   t->M = static_cast<uint32_t>(pow2 - 1);
   t->p = static_cast<uint32_t>(nb - pow2);
   const uint64_t want = std::max<uint64_t>(1024, (nb * kS * cfg->stash_permille + 999) / 1000);
-  t->stash_cap = static_cast<uint32_t>((want + 31) / 32 * 32);
+  t->stash_cap = static_cast<uint32_t>(std::min<uint64_t>((want + 31) / 32 * 32, 1ull << 31));
   uint64_t alloc = 1;
   while (alloc < t->stash_cap) alloc <<= 1;
   t->stash_alloc = alloc;
-  cudaError_t e = cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, t->device);
+  cudaError_t e = cudaGetDevice(&t->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, t->device);
   if (e == cudaSuccess) e = setup32(static_cast<int>(cfg->layout), &t->blocks_per_sm);
   if (e == cudaSuccess) e = cudaMalloc(&t->buckets, nb * kS * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->masks, nb * sizeof(uint32_t));

@@ -76,7 +76,8 @@ def test_host_validation_of_later_entry_points(lib):
     c32 = hive.Config32()
     lib.hive32_config_default(C.byref(c32))
     assert c32.layout == hive.KEY16_VAL16 and c32.max_evictions == 16
-    for field, bad in (("layout", 7), ("slots", 16), ("max_evictions", 0), ("lock_spin_limit", 0)):
+    for field, bad in (("layout", 7), ("slots", 16), ("max_evictions", 0), ("lock_spin_limit", 0),
+                       ("stash_permille", 1001)):
         b = hive.Config32()
         lib.hive32_config_default(C.byref(b))
         setattr(b, field, bad)
