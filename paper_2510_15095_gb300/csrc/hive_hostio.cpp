@@ -64,16 +64,10 @@ hive_status ensure_staging(hive_table* t) {
 
 enum Kind { kIns, kFind, kExec };
 
-hive_status run_host(hive_table* t, Kind kind, const uint8_t* h_ops, const uint32_t* h_keys,
-                     const uint32_t* h_vals, uint64_t n, uint32_t* h_out, uint8_t* h_st,
-                     cudaStream_t s) {
-  if (!t) return hfail(HIVE_ERR_INVALID_ARG, "table is NULL");
-  if (n >= (1ull << 32)) return hfail(HIVE_ERR_INVALID_ARG, "n must be below 2^32 per call");
-  if (n == 0) return HIVE_OK;
-  if (!h_keys || (kind == kIns && !h_vals) || (kind == kFind && !h_out) || (kind == kExec && !h_ops))
-    return hfail(HIVE_ERR_INVALID_ARG, "a required host array is NULL");
-  hive_status st = ensure_staging(t);
-  if (st != HIVE_OK) return st;
+hive_status run_chunks(hive_table* t, Kind kind, const uint8_t* h_ops, const uint32_t* h_keys,
+                       const uint32_t* h_vals, uint64_t n, uint32_t* h_out, uint8_t* h_st,
+                       cudaStream_t s) {
+  hive_status st = HIVE_OK;
   HostIO& io = t->io;
   const uint64_t chunks = (n + kChunkOps - 1) / kChunkOps;
   for (uint64_t c = 0; c < chunks; ++c) {
@@ -107,6 +101,28 @@ hive_status run_host(hive_table* t, Kind kind, const uint8_t* h_ops, const uint3
   }
   HCK(cudaStreamSynchronize(io.down));
   return HIVE_OK;
+}
+
+hive_status run_host(hive_table* t, Kind kind, const uint8_t* h_ops, const uint32_t* h_keys,
+                     const uint32_t* h_vals, uint64_t n, uint32_t* h_out, uint8_t* h_st,
+                     cudaStream_t s) {
+  if (!t) return hfail(HIVE_ERR_INVALID_ARG, "table is NULL");
+  if (n >= (1ull << 32)) return hfail(HIVE_ERR_INVALID_ARG, "n must be below 2^32 per call");
+  if (n == 0) return HIVE_OK;
+  if (!h_keys || (kind == kIns && !h_vals) || (kind == kFind && !h_out) || (kind == kExec && !h_ops))
+    return hfail(HIVE_ERR_INVALID_ARG, "a required host array is NULL");
+  hive_status st = ensure_staging(t);
+  if (st != HIVE_OK) return st;
+  st = run_chunks(t, kind, h_ops, h_keys, h_vals, n, h_out, h_st, s);
+  if (st != HIVE_OK) {
+    // an error part-way leaves copies of earlier chunks queued: finish them
+    // before returning, so that no copy touches the caller's host arrays
+    // after the call (the error text already set is kept)
+    cudaStreamSynchronize(t->io.up);
+    cudaStreamSynchronize(t->io.down);
+    cudaGetLastError();
+  }
+  return st;
 }
 
 }  // namespace
