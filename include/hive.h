@@ -428,6 +428,28 @@ hive_status hive32_stats(hive32_table* t, hive_stats_t* out, void* stream);
 /* Host image; with img->buckets == NULL only the scalar fields are filled. */
 hive_status hive32_dump(hive32_table* t, hive32_image* img, void* stream);
 
+/* ---- Batch-contract check (a debugging aid; the paper has none) ----
+ * Section III-D runs the ops of a batch concurrently, so a batch has one
+ * result only under the batch contract above.  This checks it on HOST
+ * arrays: h_keys[n], and h_ops[n] (HIVE_OP_* codes) for a mixed batch.  With
+ * h_ops NULL every op is `op`: HIVE_OP_INSERT or HIVE_OP_ERASE for an
+ * insert or erase batch, HIVE_OP_FIND for a find batch (which always
+ * passes).  Ops whose key is >= key_limit touch nothing and are ignored: pass
+ * 0xFFFFFFFE for 32-bit keys, 0xFFFE for HIVE32_KEY16_VAL16.  Unknown op
+ * codes count as finds, as in the kernels.  Returns HIVE_OK, or
+ * HIVE_ERR_INVALID_ARG with *first_bad (nullable; n when the batch passes)
+ * = the smallest i such that ops [0, i] already break the contract, and an
+ * error text naming the key.  Cost: a two-pass radix sort of the keys.
+ *
+ * With the environment variable HIVE_DEBUG set (to anything but "0") when a
+ * table is created, every update call on it (insert, erase, execute, their
+ * 32-bit, allocation-free and host-buffer forms) first copies its key and
+ * op arrays to the host on `stream`, waits, and runs this check; a batch
+ * that fails returns HIVE_ERR_INVALID_ARG and queues nothing.  Multi-table
+ * batches are not checked. */
+hive_status hive_check_batch(const uint8_t* h_ops, uint32_t op, const uint32_t* h_keys, uint64_t n,
+                             uint32_t key_limit, uint64_t* first_bad);
+
 /* Text of the calling thread's last error (never NULL). */
 const char* hive_last_error(void);
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhive_gb300.so")
 SOURCES = ["hive_kernels.cu", "hive32_kernels.cu", "hive_host.cpp", "hive32.cpp", "hive_multi.cpp",
-           "hive_hostio.cpp", "hive_vmm.cpp", "hive_noalloc.cu"]
+           "hive_hostio.cpp", "hive_vmm.cpp", "hive_contract.cpp", "hive_noalloc.cu"]
 HEADERS = ["hive_internal.h", "hive_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -34,6 +34,7 @@ struct hive32_table {
   uint32_t* list_idx = nullptr;
   uint64_t list_cap = 0;
   int num_sms = 0, blocks_per_sm = 1;
+  bool check_contract = false;  // HIVE_DEBUG at creation: update calls check the batch contract
 };
 
 namespace {
@@ -122,6 +123,14 @@ hive_status run32(hive32_table* t, int mode, const uint8_t* ops, const uint32_t*
   if (mode == kModeInsert && !vals && t->cfg.layout != HIVE32_KEY_ONLY)
     return fail32(HIVE_ERR_INVALID_ARG, "vals must not be NULL");
   const bool ins = mode == kModeInsert || mode == kModeMixed;
+  if (t->check_contract && mode != kModeFind) {
+    const uint32_t op = mode == kModeInsert ? HIVE_OP_INSERT : mode == kModeErase ? HIVE_OP_ERASE
+                                                                                  : HIVE_OP_FIND;
+    const uint32_t key_limit = t->cfg.layout == HIVE32_KEY16_VAL16 ? 0xFFFEu : 0xFFFFFFFEu;
+    if ((st = check_contract_device(mode == kModeMixed ? ops : nullptr, op, keys, n, key_limit, s)) !=
+        HIVE_OK)
+      return st;
+  }
   if (ins && (st = ensure_list32(t, n)) != HIVE_OK) return st;
   const View32 v = view32(t);
   const Ops32 a{ops, keys, vals, vals_out, found, status};
@@ -171,6 +180,7 @@ hive_status hive32_create(const hive32_config* cfg, void* stream, hive32_table**
   hive32_table* t = new (std::nothrow) hive32_table();
   if (!t) return fail32(HIVE_ERR_OOM, "host allocation failed");
   t->cfg = *cfg;
+  t->check_contract = contract_check_env();
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   t->nb = nb;
   uint64_t pow2 = 1;

@@ -450,6 +450,7 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
   hive_table* t = new (std::nothrow) hive_table();
   if (!t) return fail(HIVE_ERR_OOM, "host allocation failed");
   t->cfg = *cfg;
+  t->check_contract = contract_check_env();
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const uint32_t S = cfg->bucket_slots;
   t->S = S;
@@ -548,6 +549,9 @@ hive_status hive_insert(hive_table* t, const uint32_t* keys, const uint32_t* val
   if (n == 0) return HIVE_OK;
   if (!keys || !vals) return fail(HIVE_ERR_INVALID_ARG, "keys and vals must not be NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (t->check_contract &&
+      (st = check_contract_device(nullptr, HIVE_OP_INSERT, keys, n, kReservedKeyMin, s)) != HIVE_OK)
+    return st;
   if ((st = ensure_lists(t, n)) != HIVE_OK) return st;
   if (t->cfg.resizable && (st = grow_for(t, n, s)) != HIVE_OK) return st;
   const View v = make_view(t);
@@ -583,6 +587,9 @@ hive_status hive_erase(hive_table* t, const uint32_t* keys, uint64_t n, uint8_t*
   if (n == 0) return HIVE_OK;
   if (!keys) return fail(HIVE_ERR_INVALID_ARG, "keys must not be NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (t->check_contract &&
+      (st = check_contract_device(nullptr, HIVE_OP_ERASE, keys, n, kReservedKeyMin, s)) != HIVE_OK)
+    return st;
   const View v = make_view(t);
   HIVE_LAUNCH(t, HIVE_K_ERASE, s,
               launch_ops(kModeErase, v, nullptr, keys, nullptr, n, nullptr, nullptr, status,
@@ -604,6 +611,9 @@ hive_status hive_execute(hive_table* t, const uint8_t* ops, const uint32_t* keys
   if (n == 0) return HIVE_OK;
   if (!ops || !keys) return fail(HIVE_ERR_INVALID_ARG, "ops and keys must not be NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (t->check_contract &&
+      (st = check_contract_device(ops, HIVE_OP_FIND, keys, n, kReservedKeyMin, s)) != HIVE_OK)
+    return st;
   if ((st = ensure_lists(t, n)) != HIVE_OK) return st;
   if (t->cfg.resizable) {
     HIVE_CK(cudaMemsetAsync(&t->ctrl->n_insert, 0, sizeof(unsigned), s));
@@ -631,6 +641,9 @@ hive_status hive_execute_fused(hive_table* t, const uint8_t* ops, const uint32_t
   if (n == 0) return HIVE_OK;
   if (!ops || !keys) return fail(HIVE_ERR_INVALID_ARG, "ops and keys must not be NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (t->check_contract &&
+      (st = check_contract_device(ops, HIVE_OP_FIND, keys, n, kReservedKeyMin, s)) != HIVE_OK)
+    return st;
   if ((st = ensure_lists(t, n)) != HIVE_OK) return st;
   if (t->cfg.resizable) {
     HIVE_CK(cudaMemsetAsync(&t->ctrl->n_insert, 0, sizeof(unsigned), s));

@@ -111,8 +111,16 @@ hive_status run_host(hive_table* t, Kind kind, const uint8_t* h_ops, const uint3
   if (n == 0) return HIVE_OK;
   if (!h_keys || (kind == kIns && !h_vals) || (kind == kFind && !h_out) || (kind == kExec && !h_ops))
     return hfail(HIVE_ERR_INVALID_ARG, "a required host array is NULL");
-  hive_status st = ensure_staging(t);
-  if (st != HIVE_OK) return st;
+  hive_status st = HIVE_OK;
+  if (t->check_contract && kind != kFind) {
+    // the chunks are checked one by one as well; this catches a key repeated
+    // across chunks
+    uint64_t bad = 0;
+    st = hive_check_batch(kind == kExec ? h_ops : nullptr, HIVE_OP_INSERT, h_keys, n,
+                          kReservedKeyMin, &bad);
+    if (st != HIVE_OK) return st;
+  }
+  if ((st = ensure_staging(t)) != HIVE_OK) return st;
   st = run_chunks(t, kind, h_ops, h_keys, h_vals, n, h_out, h_st, s);
   if (st != HIVE_OK) {
     // an error part-way leaves copies of earlier chunks queued: finish them

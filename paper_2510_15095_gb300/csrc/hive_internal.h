@@ -256,6 +256,7 @@ struct hive_table {
   HostIO io;  // host-buffer call staging (allocated on first use)
   hive::GrowArray bucket_vm;  // resizable tables: buckets on virtual memory
   bool vmm = false;
+  bool check_contract = false;  // HIVE_DEBUG at creation: update calls check the batch contract
 };
 
 // Helpers shared by the translation units of the library (hive_host.cpp
@@ -280,4 +281,10 @@ void free_staging(hive_table* t);  // releases the host-buffer call staging
 hive_status ensure_committed(hive_table* t, cudaStream_t s);
 bool table_view(const hive_table* t, View* v, Launch* L, bool* resizable);
 void set_last_error(const std::string& msg);  // text returned by hive_last_error()
+// Batch-contract debugging (hive_contract.cpp): whether HIVE_DEBUG asks for
+// the check, and the check of a batch whose arrays the GPU addresses (copied
+// to the host on `s` first).
+bool contract_check_env();
+hive_status check_contract_device(const uint8_t* ops, uint32_t op, const uint32_t* keys,
+                                  uint64_t n, uint32_t key_limit, cudaStream_t s);
 }  // namespace hive

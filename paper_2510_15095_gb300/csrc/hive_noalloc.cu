@@ -86,6 +86,11 @@ extern "C" hive_status hive_insert_noalloc(hive_table* t, const uint32_t* keys,
   if (!keys || !vals)
     return noalloc_fail(HIVE_ERR_INVALID_ARG, "hive_insert_noalloc: keys and vals must not be NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (t->check_contract) {  // HIVE_DEBUG (host memory only)
+    const hive_status st =
+        hive::check_contract_device(nullptr, HIVE_OP_INSERT, keys, n, hive::kReservedKeyMin, s);
+    if (st != HIVE_OK) return st;
+  }
   NoAllocScratch* sc = nullptr;
   cudaError_t e = scratch_address(&sc);
   if (e != cudaSuccess)

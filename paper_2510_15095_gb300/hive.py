@@ -32,7 +32,7 @@ EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", 
            "hive_stats", "hive_dump", "hive_profile_enable", "hive_profile_read",
            "hive_insert_noalloc", "hive_multi_create", "hive_multi_execute",
            "hive_multi_destroy", "hive_insert_host", "hive_find_host", "hive_execute_host",
-           "hive_reserve", "hive_memory", "hive_last_error",
+           "hive_reserve", "hive_memory", "hive_check_batch", "hive_last_error",
            "hive32_config_default", "hive32_create", "hive32_destroy", "hive32_insert",
            "hive32_find", "hive32_erase", "hive32_execute", "hive32_size", "hive32_clear",
            "hive32_check",
@@ -150,6 +150,7 @@ def load_library(path: str = LIB_PATH):
         L.hive32_clear.argtypes = [vp, vp]
         L.hive32_stats.argtypes = [vp, C.POINTER(Stats), vp]
         L.hive32_dump.argtypes = [vp, C.POINTER(Image32), vp]
+        L.hive_check_batch.argtypes = [vp, C.c_uint32, vp, u64, C.c_uint32, C.POINTER(u64)]
         L.hive_last_error.argtypes = []
         L.hive_last_error.restype = C.c_char_p
         for name in EXPORTS:
@@ -561,6 +562,29 @@ class HiveMulti:
             self.close()
         except Exception:
             pass
+
+
+def check_batch(keys, ops=None, op: int = OP_INSERT, key_limit: int = 0xFFFFFFFE):
+    """Host-side batch-contract check (hive_check_batch): None when the batch
+    keeps the contract, else the index of the first op that breaks it.
+    `keys` (and `ops`, for a mixed batch) are host arrays (numpy or CPU
+    tensors); with ops None every op is `op`.  Needs no GPU."""
+    L = load_library()
+    a = np.asarray(keys)
+    # 32-bit integer storage is taken as unsigned bits; anything else is converted
+    k = np.ascontiguousarray(a.view(np.uint32) if a.dtype.kind in "iu" and a.dtype.itemsize == 4
+                             else a.astype(np.uint32))
+    o = None if ops is None else np.ascontiguousarray(np.asarray(ops, dtype=np.uint8))
+    if o is not None and o.size != k.size:
+        raise ValueError("ops and keys differ in length")
+    bad = C.c_uint64()
+    code = L.hive_check_batch(None if o is None else o.ctypes.data, op, k.ctypes.data, k.size,
+                              key_limit, C.byref(bad))
+    if code == HIVE_OK:
+        return None
+    if code != 1 or bad.value >= k.size:
+        _raise(L, code)
+    return int(bad.value)
 
 
 def to_device_u32(a: np.ndarray, device="cuda"):
