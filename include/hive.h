@@ -445,8 +445,11 @@ hive_status hive32_dump(hive32_table* t, hive32_image* img, void* stream);
  * table is created, every update call on it (insert, erase, execute, their
  * 32-bit, allocation-free and host-buffer forms) first copies its key and
  * op arrays to the host on `stream`, waits, and runs this check; a batch
- * that fails returns HIVE_ERR_INVALID_ARG and queues nothing.  Multi-table
- * batches are not checked. */
+ * that fails returns HIVE_ERR_INVALID_ARG and queues nothing.  In a
+ * multi-table batch (hive_multi_execute) each such table is checked over
+ * all of its segments of the batch, in segment order, and the error text
+ * names the table.  The check waits on `stream`, so a debug table makes
+ * every update call synchronous. */
 hive_status hive_check_batch(const uint8_t* h_ops, uint32_t op, const uint32_t* h_keys, uint64_t n,
                              uint32_t key_limit, uint64_t* first_bad);
 

@@ -8,9 +8,9 @@
 // that the ops of one key stay in array order, then walks each group.
 //
 // With HIVE_DEBUG set in the environment when a table is created, every
-// update call on it first copies its key and op arrays to the host and runs
-// this check; a batch that fails returns HIVE_ERR_INVALID_ARG and queues
-// nothing.
+// update call on it (multi-table batches included) first copies its key and
+// op arrays to the host and runs this check; a batch that fails returns
+// HIVE_ERR_INVALID_ARG and queues nothing.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -108,6 +108,34 @@ MultiJob* jobs_of(hive_multi* m, uint8_t* base) {
   return reinterpret_cast<MultiJob*>(base + m->off_jobs);
 }
 
+// HIVE_DEBUG tables: the batch contract holds per table, over all of its
+// segments of the batch taken in order.  Copies those keys and op codes to
+// the host (waiting on `s`) and checks them with hive_check_batch.
+hive_status check_table_segments(const hive_segment* segs, uint32_t n_segs, uint32_t tb,
+                                 cudaStream_t s) {
+  uint64_t total = 0;
+  for (uint32_t i = 0; i < n_segs; ++i)
+    if (segs[i].table == tb) total += segs[i].n;
+  if (total >= (1ull << 32))
+    return mfail(HIVE_ERR_INVALID_ARG, "a table's segments hold 2^32 ops or more");
+  std::vector<uint32_t> hk(total);
+  std::vector<uint8_t> ho(total);
+  uint64_t at = 0;
+  for (uint32_t i = 0; i < n_segs; ++i) {
+    const hive_segment& g = segs[i];
+    if (g.table != tb || !g.n) continue;
+    MCK(cudaMemcpyAsync(hk.data() + at, g.keys, g.n * sizeof(uint32_t), cudaMemcpyDefault, s));
+    MCK(cudaMemcpyAsync(ho.data() + at, g.ops, g.n, cudaMemcpyDefault, s));
+    at += g.n;
+  }
+  MCK(cudaStreamSynchronize(s));
+  uint64_t bad = 0;
+  const hive_status st =
+      hive_check_batch(ho.data(), HIVE_OP_FIND, hk.data(), total, kReservedKeyMin, &bad);
+  if (st != HIVE_OK) set_last_error("table " + std::to_string(tb) + ": " + hive_last_error());
+  return st;
+}
+
 // The fixed part of a batch; `s` is the caller's stream or the capture stream.
 hive_status enqueue_fixed(hive_multi* m, cudaStream_t s) {
   const List ovf{m->ovf_words, m->ovf_idx, m->d_count, m->ovf_seg};
@@ -259,6 +287,11 @@ hive_status hive_multi_execute(hive_multi* m, const hive_segment* segs, uint32_t
     }
   }
   if (total_ops > m->max_ops) return mfail(HIVE_ERR_INVALID_ARG, "batch larger than max_ops");
+  for (uint32_t tb : touched) {
+    if (!m->tables[tb]->check_contract) continue;
+    hive_status st = check_table_segments(segs, n_segs, tb, s);
+    if (st != HIVE_OK) return st;
+  }
 
   // The slot of this batch: wait until the batch that used it two calls ago
   // is done (its staging buffer is then free).

@@ -75,3 +75,32 @@ def test_debug_hive32_rejects_broken_batches(H, monkeypatch):
     assert s.insert(i32([70000, 70001])).cpu().tolist() == [H.INSERTED] * 2
     assert s.size() == 2
     s.close()
+
+
+def test_debug_multi_table_batch(H, monkeypatch):
+    """The contract holds per table over all of its segments of a batch; one
+    key in two different tables is fine."""
+    monkeypatch.setenv("HIVE_DEBUG", "1")
+    ta, tb = H.HiveTable(1 << 12), H.HiveTable(1 << 12)
+    m = H.HiveMulti([ta, tb], max_segments=4, max_ops=1 << 10, use_graph=False)
+
+    def seg(t, ops, keys, vals):
+        n = len(keys)
+        return {"table": t, "ops": u8(ops), "keys": i32(keys), "vals": i32(vals),
+                "vals_out": torch.empty(n, dtype=torch.int32, device="cuda"),
+                "status": torch.empty(n, dtype=torch.uint8, device="cuda")}
+
+    with pytest.raises(H.HiveError) as e:
+        m.execute([seg(0, [H.OP_INSERT], [5], [1]), seg(1, [H.OP_INSERT], [5], [2]),
+                   seg(0, [H.OP_FIND], [5], [0])])
+    assert e.value.code == 1 and "table 0" in str(e.value)
+    assert ta.size() == 0 and tb.size() == 0
+    g = [seg(0, [H.OP_INSERT], [5], [1]), seg(1, [H.OP_INSERT, H.OP_FIND], [5, 6], [2, 0])]
+    m.execute(g)
+    torch.cuda.synchronize()
+    assert g[0]["status"].cpu().tolist() == [H.INSERTED]
+    assert g[1]["status"].cpu().tolist() == [H.INSERTED, H.NOT_FOUND]
+    assert ta.size() == 1 and tb.size() == 1
+    m.close()
+    ta.close()
+    tb.close()
