@@ -57,3 +57,41 @@ def test_mixed_batch_contract():
     assert not np.isin(finds, upd).any()
     assert np.isin(keys[ops == W.OP_ERASE], live).all()
     assert not np.isin(keys[ops == W.OP_INSERT], live).any()
+
+
+def _inv_xorshift(y, s):
+    x = y
+    for _ in range(32 // s + 1):
+        x = y ^ (x >> s)
+    return x & 0xFFFFFFFF
+
+
+def test_splitmix32_undoes_step_by_step():
+    """The value generator is the golden-ratio increment followed by the
+    MurmurHash3 finalizer; undoing each published step in reverse order must
+    give the input back (a wrong constant, shift or order breaks it)."""
+    xs = np.array([0, 1, 2, 0x61C88646, 0x61C88647, 0xFFFFFFFF, 0xDEADBEEF]
+                  + np.random.default_rng(3).integers(0, 1 << 32, 3000).tolist(), np.uint64)
+    ys = W.splitmix32(xs)
+    m = 1 << 32
+    for x, y in zip(xs.tolist(), ys.tolist()):
+        z = _inv_xorshift(int(y), 16)
+        z = (z * pow(0xC2B2AE35, -1, m)) % m
+        z = _inv_xorshift(z, 13)
+        z = (z * pow(0x85EBCA6B, -1, m)) % m
+        z = _inv_xorshift(z, 16)
+        assert (z - 0x9E3779B9) % m == x
+    assert int(W.splitmix32(np.array([(1 << 32) - 0x9E3779B9]))[0]) == 0  # fmix32(0) = 0
+
+
+def test_torch_generators_match_numpy():
+    torch = pytest.importorskip("torch")
+    x = np.concatenate([np.arange(0, 5000, dtype=np.uint64),
+                        np.random.default_rng(4).integers(0, 1 << 32, 20000).astype(np.uint64),
+                        np.array([(1 << 32) - 1, (1 << 32) - 2], np.uint64)])
+    xt = torch.from_numpy(x.astype(np.int64))
+    assert np.array_equal(W.splitmix32_t(xt).numpy().astype(np.uint64), W.splitmix32(x).astype(np.uint64))
+    for bits in (16, 32):
+        xb = x & np.uint64((1 << bits) - 1)
+        got = W.feistel_bits_t(torch.from_numpy(xb.astype(np.int64)), 9, bits).numpy()
+        assert np.array_equal(got.astype(np.uint64), W.feistel_bits(xb, 9, bits).astype(np.uint64))
