@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -26,6 +27,11 @@ namespace hive {
 namespace {
 
 bool is_update(uint32_t op) { return op == HIVE_OP_INSERT || op == HIVE_OP_ERASE; }
+
+hive_status host_oom() {
+  set_last_error("batch contract check: host allocation failed");
+  return HIVE_ERR_OOM;
+}
 
 // Indices of the ops whose key is below key_limit, stably sorted by key
 // (the ops of one key keep their array order).
@@ -62,8 +68,14 @@ bool contract_check_env() {
 hive_status check_contract_device(const uint8_t* ops, uint32_t op, const uint32_t* keys,
                                   uint64_t n, uint32_t key_limit, cudaStream_t s) {
   if (n == 0) return HIVE_OK;
-  std::vector<uint32_t> hk(n);
-  std::vector<uint8_t> ho(ops ? n : 0);
+  std::vector<uint32_t> hk;
+  std::vector<uint8_t> ho;
+  try {
+    hk.resize(n);
+    ho.resize(ops ? n : 0);
+  } catch (const std::bad_alloc&) {
+    return host_oom();
+  }
   cudaError_t e = cudaMemcpyAsync(hk.data(), keys, n * sizeof(uint32_t), cudaMemcpyDefault, s);
   if (e == cudaSuccess && ops) e = cudaMemcpyAsync(ho.data(), ops, n, cudaMemcpyDefault, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -92,7 +104,12 @@ extern "C" hive_status hive_check_batch(const uint8_t* h_ops, uint32_t op, const
     return HIVE_ERR_INVALID_ARG;
   }
   if (!h_ops && !hive::is_update(op)) return HIVE_OK;  // a find batch always passes
-  const std::vector<uint32_t> idx = hive::sorted_by_key(h_keys, n, key_limit);
+  std::vector<uint32_t> idx;
+  try {
+    idx = hive::sorted_by_key(h_keys, n, key_limit);
+  } catch (const std::bad_alloc&) {
+    return hive::host_oom();
+  }
   // a group is the ops of one key in array order; the first op that makes
   // the prefix [0, i] break the contract is the second update of a key, or
   // an update after a find of it, or a find after an update of it

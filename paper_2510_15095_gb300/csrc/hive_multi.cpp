@@ -118,8 +118,14 @@ hive_status check_table_segments(const hive_segment* segs, uint32_t n_segs, uint
     if (segs[i].table == tb) total += segs[i].n;
   if (total >= (1ull << 32))
     return mfail(HIVE_ERR_INVALID_ARG, "a table's segments hold 2^32 ops or more");
-  std::vector<uint32_t> hk(total);
-  std::vector<uint8_t> ho(total);
+  std::vector<uint32_t> hk;
+  std::vector<uint8_t> ho;
+  try {
+    hk.resize(total);
+    ho.resize(total);
+  } catch (const std::bad_alloc&) {
+    return mfail(HIVE_ERR_OOM, "batch contract check: host allocation failed");
+  }
   uint64_t at = 0;
   for (uint32_t i = 0; i < n_segs; ++i) {
     const hive_segment& g = segs[i];
