@@ -123,3 +123,23 @@ def test_resize_stream_batches_keep_the_contract(H):
         ins, er = ((2, 5), (1, 5)) if b < 2 else ((1, 5), (2, 5))  # growth, then shrink
         ops, keys, _, live, ctr = W.stream_step_t(torch, 11, live, ctr, 1 << 14, "cpu", ins, er)
         assert H.check_batch(keys.numpy(), ops=ops.numpy()) is None
+
+
+def test_serving_trace_requests_keep_the_contract(H):
+    """Each request of the serving trace is one batch on its table (the server
+    puts at most one request per table in a multi-table batch)."""
+    torch = pytest.importorskip("torch")
+    from paper_2510_15095_gb300 import serving as SV
+    counts = [1 << 12] * 4
+    before = list(counts)
+    reqs = SV.make_trace(torch, 4, 40, rate_per_s=1000.0, seed=9, counts=counts, max_log2_ops=12,
+                         device="cpu")
+    arr = [r.arrival for r in reqs]
+    assert arr[0] == 0.0 and all(b >= a for a, b in zip(arr, arr[1:]))
+    added = [0] * 4
+    for r in reqs:
+        assert 0 <= r.table < 4 and 1 <= r.n <= 1 << 12
+        assert int((r.ops == OP_INSERT).sum()) == r.n_insert
+        added[r.table] += r.n_insert
+        assert H.check_batch(r.keys.numpy(), ops=r.ops.numpy()) is None
+    assert [c - b for c, b in zip(counts, before)] == added
