@@ -399,7 +399,8 @@ typedef struct {
 
 void hive32_config_default(hive32_config* cfg);
 /* Allocates the table (buckets, masks, locks, stash) on the current device.
- * Errors: INVALID_ARG for a bad layout or size; OOM. */
+ * Errors: INVALID_ARG for a bad layout, size, max_evictions, stash_permille
+ * or lock_spin_limit; OOM. */
 hive_status hive32_create(const hive32_config* cfg, void* stream, hive32_table** out);
 hive_status hive32_destroy(hive32_table* t);
 /* Insert/Replace (vals may be NULL for HIVE32_KEY_ONLY); status nullable:
