@@ -139,6 +139,7 @@ enum {
   HIVE_K_MERGE = 7,    /* linear-hashing merge and its pre-check */
   HIVE_K_COUNT = 8,    /* insert counting for a resizable mixed batch */
   HIVE_K_FUSED = 9,    /* single-kernel mixed batch (hive_execute_fused) */
+  HIVE_K_CLAIM = 10,   /* claims of a mixed batch's new keys (step 2) */
   HIVE_K_KINDS = 16
 };
 

@@ -118,7 +118,9 @@ View hive::make_view(const hive_table* t) {
 
 namespace {
 
-List list_a(const hive_table* t) { return List{t->la_words, t->la_idx, &t->ctrl->ovf_n}; }
+List list_a(const hive_table* t) {
+  return List{t->la_words, t->la_idx, &t->ctrl->ovf_n, nullptr, t->la_cnt};
+}
 List list_b(const hive_table* t) { return List{t->lb_words, t->lb_idx, &t->ctrl->pend_n}; }
 
 void free_lists(hive_table* t) {
@@ -126,28 +128,34 @@ void free_lists(hive_table* t) {
   cudaFree(t->la_idx);
   cudaFree(t->lb_words);
   cudaFree(t->lb_idx);
+  cudaFree(t->la_cnt);
+  t->la_cnt = nullptr;
   t->la_words = t->lb_words = nullptr;
   t->la_idx = t->lb_idx = nullptr;
-  t->list_cap = 0;
+  t->list_cap = t->lb_cap = 0;
 }
 
 // The op lists hold at most one entry per op of a call (or per word of a
 // merge batch), so they grow to the largest call seen.
-hive_status ensure_lists(hive_table* t, uint64_t n) {
-  if (n <= t->list_cap) return HIVE_OK;
-  const uint64_t cap = std::max<uint64_t>(next_pow2(n), 1u << 16);
+// List B exists for resizable tables (pending items) and once a mixed batch
+// has run (its claim kernel hands full-bucket items from A to B).
+hive_status ensure_lists(hive_table* t, uint64_t n, bool need_b = false) {
+  const bool two = t->cfg.resizable != 0 || need_b || t->lb_cap != 0;
+  if (n <= t->list_cap && (!two || n <= t->lb_cap)) return HIVE_OK;
+  const uint64_t cap = std::max<uint64_t>(next_pow2(std::max(n, t->list_cap)), 1u << 16);
   HIVE_CK(cudaDeviceSynchronize());
   free_lists(t);
-  const bool two = t->cfg.resizable != 0;
   cudaError_t e = cudaMalloc(&t->la_words, cap * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&t->la_idx, cap * sizeof(uint32_t));
   if (e == cudaSuccess && two) e = cudaMalloc(&t->lb_words, cap * sizeof(uint64_t));
   if (e == cudaSuccess && two) e = cudaMalloc(&t->lb_idx, cap * sizeof(uint32_t));
+  if (e == cudaSuccess && two) e = cudaMalloc(&t->la_cnt, cap / 32);
   if (e != cudaSuccess) {
     free_lists(t);
     return cuda_fail(e, "allocating op lists");
   }
   t->list_cap = cap;
+  t->lb_cap = two ? cap : 0;
   return HIVE_OK;
 }
 
@@ -234,11 +242,12 @@ hive_status grow_for(hive_table* t, uint64_t n_ins, cudaStream_t s) {
 // After P1+P2 on a resizable table: place items that found no room by growing,
 // then run maintenance, read the size back, and contract while under the lower
 // threshold.  `status` receives FULL for ops that still find no room at
-// nb_max.
-hive_status finish_resizable(hive_table* t, uint8_t* status, cudaStream_t s) {
+// nb_max.  The pending items are in list B, or in list A with !pending_in_b.
+hive_status finish_resizable(hive_table* t, uint8_t* status, cudaStream_t s,
+                             bool pending_in_b = true) {
   hive_status st = readback(t, s);
   if (st != HIVE_OK) return st;
-  bool in_b = true;  // pending items are in list B
+  bool in_b = pending_in_b;
   while ((in_b ? t->host_ctrl->pend_n : t->host_ctrl->ovf_n) != 0) {
     bool did = false;
     st = split_step(t, s, &did);
@@ -614,7 +623,7 @@ hive_status hive_execute(hive_table* t, const uint8_t* ops, const uint32_t* keys
   if (t->check_contract &&
       (st = check_contract_device(ops, HIVE_OP_FIND, keys, n, kReservedKeyMin, s)) != HIVE_OK)
     return st;
-  if ((st = ensure_lists(t, n)) != HIVE_OK) return st;
+  if ((st = ensure_lists(t, n, true)) != HIVE_OK) return st;
   if (t->cfg.resizable) {
     HIVE_CK(cudaMemsetAsync(&t->ctrl->n_insert, 0, sizeof(unsigned), s));
     HIVE_LAUNCH(t, HIVE_K_COUNT, s, launch_count_inserts(ops, n, &t->ctrl->n_insert, s));
@@ -622,12 +631,20 @@ hive_status hive_execute(hive_table* t, const uint8_t* ops, const uint32_t* keys
     if ((st = grow_for(t, t->host_ctrl->n_insert, s)) != HIVE_OK) return st;
   }
   const View v = make_view(t);
+  // P1: finds, erases and replaces; the new keys are listed in A (reading 14:
+  // no op of P1 moves a word, and the claims of P2 see every slot P1 freed)
   HIVE_LAUNCH(t, HIVE_K_MIXED, s,
               launch_ops(kModeMixed, v, ops, keys, vals, n, vals_out, nullptr, status,
                          list_a(t), t->L, s));
+  // P2: claims (A -> B for both-full buckets), then eviction and stash (B,
+  // with pending items back to A)
+  HIVE_CK(cudaMemsetAsync(&t->ctrl->pend_n, 0, sizeof(unsigned), s));
+  HIVE_LAUNCH(t, HIVE_K_CLAIM, s, launch_claim(v, list_a(t), n, list_b(t), status, t->L, s));
+  HIVE_CK(cudaMemsetAsync(&t->ctrl->ovf_n, 0, sizeof(unsigned), s));
   HIVE_LAUNCH(t, HIVE_K_EVICT, s,
-              launch_overflow(v, list_a(t), list_b(t), t->cfg.resizable, status, t->L, s));
-  if (t->cfg.resizable) return finish_resizable(t, status, s);
+              launch_overflow(v, list_b(t), list_a(t), t->cfg.resizable, status, t->L, s));
+  HIVE_CK(cudaMemsetAsync(&t->ctrl->pend_n, 0, sizeof(unsigned), s));
+  if (t->cfg.resizable) return finish_resizable(t, status, s, false);
   HIVE_LAUNCH(t, HIVE_K_MAINT, s, launch_maintenance(v, s));
   return HIVE_OK;
 }
@@ -701,7 +718,7 @@ hive_status hive_memory(hive_table* t, uint64_t* committed, uint64_t* reserved) 
   const uint64_t bucket_now = t->vmm ? t->bucket_vm.committed : bucket_max;
   const uint64_t other = t->nb_max * 3 * sizeof(uint32_t) + t->stash_alloc * sizeof(uint64_t) +
                          t->stash_cap * sizeof(uint32_t) + sizeof(Ctrl) +
-                         t->list_cap * (t->cfg.resizable ? 24 : 12);
+                         (t->list_cap + t->lb_cap) * 12 + t->lb_cap / 32;
   *committed = bucket_now + other;
   *reserved = bucket_max + other;
   return HIVE_OK;

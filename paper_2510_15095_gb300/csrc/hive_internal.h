@@ -87,6 +87,7 @@ struct List {
   uint32_t* idx;   // caller op index or kNoOp
   unsigned int* count;
   uint32_t* seg;   // multi-table batches: segment of each entry (else NULL)
+  uint8_t* chunk_cnt;  // mixed batches: new keys of each 32-op chunk (see k_claim)
 };
 
 // One (table, op range) of a multi-table batch; 64 bytes.
@@ -126,6 +127,7 @@ struct Launch {
   int fused_blocks_per_sm;   // single-kernel mixed batch
   int ovf_blocks_per_sm;
   int multi_blocks_per_sm;
+  int claim_blocks_per_sm;   // claims of a mixed batch's new keys
 };
 
 // Kernel launchers (hive_kernels.cu).  Each returns the launch error.
@@ -134,6 +136,10 @@ cudaError_t launch_ops(int mode, const View& v, const uint8_t* ops, const uint32
                        uint8_t* status, List ovf, const Launch& L, cudaStream_t s);
 cudaError_t launch_overflow(const View& v, List in, List pend, int resizable, uint8_t* status,
                             const Launch& L, cudaStream_t s);
+// Claims for the new keys of a mixed batch of n ops, left in `in` chunk by
+// chunk by the bulk kernel; items with both buckets full go to `out`.
+cudaError_t launch_claim(const View& v, List in, uint64_t n, List out, uint8_t* status,
+                         const Launch& L, cudaStream_t s);
 cudaError_t launch_maintenance(const View& v, cudaStream_t s);
 cudaError_t launch_split(const View& v_new, uint32_t src0, uint32_t count, uint32_t half,
                          cudaStream_t s);
@@ -237,9 +243,11 @@ struct hive_table {
   uint32_t* stash_keys = nullptr;
   hive::Ctrl* ctrl = nullptr;
   hive::Ctrl* host_ctrl = nullptr;  // pinned readback buffer
-  uint64_t list_cap = 0;
+  uint64_t list_cap = 0;         // entries of list A
+  uint64_t lb_cap = 0;           // entries of list B (0: not allocated)
   uint64_t* la_words = nullptr;  // list A: bulk kernel -> eviction kernel
   uint32_t* la_idx = nullptr;
+  uint8_t* la_cnt = nullptr;     // list A per-chunk counts (mixed batches)
   uint64_t* lb_words = nullptr;  // list B: items that found no room
   uint32_t* lb_idx = nullptr;
   uint64_t size_host = 0;       // exact after each resizable call

@@ -247,8 +247,16 @@ constexpr uint32_t kMbarSpinLimit = 1u << 22;
 __host__ __device__ constexpr int stage_words(int mode, int S) {
   return mode == kModeInsert ? kStageWords : 32 * S;
 }
+// Shared-memory words per warp: its barrier, then its staging words.  (The
+// 64 KB of a paired round's block keeps three blocks within a 196 KB
+// shared-memory carveout, which leaves the L1 that the cp.async.ca copies go
+// through 60 KB; three blocks of 68 KB need the largest carveout, and the
+// insert kernel then ran at two-thirds speed.)
+__host__ __device__ constexpr int warp_smem_words(int mode, int S) {
+  return 2 + stage_words(mode, S);
+}
 __host__ __device__ constexpr size_t stage_smem(int mode, int S) {
-  return static_cast<size_t>(kOpsThreads / 32) * 8u * (stage_words(mode, S) + 2);
+  return static_cast<size_t>(kOpsThreads / 32) * 8u * warp_smem_words(mode, S);
 }
 __host__ __device__ constexpr int staged_min_blocks(int mode, int S) {
   return stage_words(mode, S) < kStageWords ? HIVE_STAGED_SMALL_MIN_BLOCKS : HIVE_STAGED_MIN_BLOCKS;
@@ -262,11 +270,11 @@ struct Stage {
 };
 
 // Sets up the calling warp's stage in the kernel's dynamic shared memory
-// (`words` staging words per warp after its barrier).
+// (`stride` words per warp: its barrier, then its staging words).
 __device__ __forceinline__ Stage stage_init(uint64_t* smem, int warp_in_block, int lane,
-                                            int words = kStageWords) {
+                                            int stride = kStageWords + 2) {
   Stage sg;
-  uint64_t* base = smem + static_cast<size_t>(warp_in_block) * (words + 2);
+  uint64_t* base = smem + static_cast<size_t>(warp_in_block) * stride;
   sg.bar = base;
   sg.buf = base + 2;
   sg.phase = 0;
@@ -671,16 +679,17 @@ __device__ __forceinline__ void scan_staged_one(const View& v, const uint64_t* s
 }
 
 // A single-bucket probe round, staged when the warp has a live stage.
-template <int MODE, int S>
+// CLAIM: the op may claim a slot in this kernel, so the round also reads the
+// bucket's free mask.
+template <int MODE, int S, bool CLAIM>
 __device__ __forceinline__ void probe_round(const View& v, unsigned need, uint32_t myb,
                                             uint32_t key, uint32_t val, uint32_t op, int lane,
                                             bool& done, uint8_t& st, uint32_t& outv,
                                             uint32_t& fcnt, uint32_t& fslot, LaneCounters& cnt,
                                             Stage* sg, PendCas& pc) {
-  constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
   if (sg && !sg->dead) {
     const bool mine = (need >> lane) & 1u;
-    const uint32_t m = (kIns && mine) ? ld_relaxed32(v.masks + myb) : 0u;
+    const uint32_t m = (CLAIM && mine && op == OP_INSERT) ? ld_relaxed32(v.masks + myb) : 0u;
     if (stage_round<S, false>(v, *sg, need, 0, myb, 0, lane)) {
       if (mine)
         scan_staged_one<MODE, S>(v, sg->buf, lane, myb, key, val, op, m, done, st, outv, fcnt,
@@ -809,6 +818,54 @@ __device__ __forceinline__ void flush_counters(const View& v, LaneCounters& cnt,
   cnt = LaneCounters();
 }
 
+// The same for every warp of a block at once, with one atomic per counter
+// and block: the counters live in one control block, and an atomic per warp
+// and counter at the end of a launch of thousands of warps queued in L2 for
+// tens of microseconds.  Every thread of the block calls it; `scratch` is
+// 8 free shared-memory words of the calling warp, and warp w's are at
+// base + w * stride.
+__device__ __forceinline__ void flush_counters_block(const View& v, LaneCounters& cnt, int lane,
+                                                     uint64_t* scratch, const uint64_t* base,
+                                                     int stride) {
+  const int sd = __reduce_add_sync(kFull, static_cast<unsigned>(cnt.size_delta));
+  const unsigned rp = __reduce_add_sync(kFull, cnt.replaced);
+  const unsigned cl = __reduce_add_sync(kFull, cnt.claimed);
+  const unsigned of = __reduce_add_sync(kFull, cnt.overflowed);
+  const unsigned sl = __reduce_add_sync(kFull, cnt.stash_lookups);
+  const unsigned rs = __ballot_sync(kFull, cnt.reserved);
+  const unsigned ct = __ballot_sync(kFull, cnt.contract);
+  __syncwarp();
+  if (lane == 0) {
+    scratch[0] = cnt.probes;
+    scratch[1] = sl;
+    scratch[2] = static_cast<uint64_t>(static_cast<int64_t>(sd));
+    scratch[3] = rp;
+    scratch[4] = cl;
+    scratch[5] = of;
+    scratch[6] = rs ? 1u : 0u;
+    scratch[7] = ct ? 1u : 0u;
+  }
+  __syncthreads();
+  const int f = threadIdx.x;
+  if (f < 8) {
+    uint64_t sum = 0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) sum += base[w * stride + f];
+    if (sum) {
+      switch (f) {
+        case 0: atomicAdd(&v.ctrl->stats[kStProbes], static_cast<unsigned long long>(sum)); break;
+        case 1: atomicAdd(&v.ctrl->stats[kStStashLookups], static_cast<unsigned long long>(sum)); break;
+        case 2: atomicAdd(&v.ctrl->size, static_cast<unsigned long long>(sum)); break;
+        case 3: atomicAdd(&v.ctrl->stats[kStReplaced], static_cast<unsigned long long>(sum)); break;
+        case 4: atomicAdd(&v.ctrl->stats[kStClaimedFast], static_cast<unsigned long long>(sum)); break;
+        case 5: atomicAdd(&v.ctrl->stats[kStOverflowed], static_cast<unsigned long long>(sum)); break;
+        case 6: atomicOr(&v.ctrl->err, kErrReserved); break;
+        default: atomicOr(&v.ctrl->err, kErrContract); break;
+      }
+    }
+  }
+  cnt = LaneCounters();
+}
+
 // One op's inputs (op code, key, value).
 struct OpIn {
   uint32_t op, key, val;
@@ -833,15 +890,61 @@ __device__ __forceinline__ OpIn load_in(const OpPtrs& a, uint32_t c, uint64_t n,
   return in;
 }
 
+// List appends at a high rate go through a per-warp shared-memory buffer: a
+// warp gathers entries over several rounds and reserves list space for all it
+// holds with one atomicAdd when the next round's entries would not fit.  One
+// counter serves the whole list; an atomicAdd on that one word per warp round
+// queued behind each other in L2 and held up every warp's memory pipeline.
+// (The bulk kernel's own eviction hand-off is rare enough to append directly;
+// a mixed batch's new keys go to fixed per-chunk places, see run_chunk.)
+constexpr int kOvfBuf = 32;
+constexpr int kOvfBufWords = kOvfBuf + kOvfBuf / 2 + kOvfBuf / 2;
+struct OvfBuf {
+  uint64_t* words;  // kOvfBuf entries each
+  uint32_t* idx;
+  uint32_t* seg;
+  uint32_t n;       // entries held (warp-uniform)
+};
+
+__device__ __forceinline__ OvfBuf ovf_buf_init(uint64_t* region) {
+  OvfBuf ob;
+  ob.words = region;
+  ob.idx = reinterpret_cast<uint32_t*>(region + kOvfBuf);
+  ob.seg = ob.idx + kOvfBuf;
+  ob.n = 0;
+  return ob;
+}
+
+// Moves every buffered entry to the list (warp-wide).
+__device__ __forceinline__ void ovf_flush(const List& ovf, OvfBuf& ob, int lane) {
+  if (!ob.n) return;
+  __syncwarp();
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(ovf.count, ob.n);
+  base = __shfl_sync(kFull, base, 0);
+  for (uint32_t j = lane; j < ob.n; j += 32) {
+    ovf.words[base + j] = ob.words[j];
+    ovf.idx[base + j] = ob.idx[j];
+    if (ovf.seg) ovf.seg[base + j] = ob.seg[j];
+  }
+  __syncwarp();
+  ob.n = 0;
+}
+
 // Ops [32c, 32c + 32) of a batch of n ops on the table of `v`.  Full-bucket
 // inserts go to the overflow list, tagged with `seg` when the list keeps tags.
 // `pre` holds the chunk's inputs when the caller loaded them ahead.
-template <int MODE, int S>
+// DEFER (mixed batches): inserts of absent keys do not claim here.  Chunk c
+// writes them to list places [32c, 32c + k) and k to ovf.chunk_cnt[c], with no
+// atomic, and k_claim places them once every find, erase and replace of the
+// batch has run.
+template <int MODE, int S, bool DEFER = false>
 __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const OpPtrs a,
                                           uint32_t c, uint64_t n, const List ovf, uint32_t seg,
                                           LaneCounters& cnt, int lane, Stage* sg = nullptr,
                                           const OpIn* pre = nullptr) {
   constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
+  constexpr bool kClaim = kIns && !DEFER;
   const uint32_t i = (c << 5) + lane;
   const bool valid = i < n;
   const OpIn in = pre ? *pre : load_in<MODE>(a, c, n, lane);
@@ -867,11 +970,13 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
   } else {
     cnt.probes += __popc(need);
     if (need)
-      probe_round<MODE, S>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt, sg, pc);
+      probe_round<MODE, S, kClaim>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt,
+                                   sg, pc);
     need = __ballot_sync(kFull, !done);
     cnt.probes += __popc(need);
     if (need)
-      probe_round<MODE, S>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt, sg, pc);
+      probe_round<MODE, S, kClaim>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt,
+                                   sg, pc);
   }
 
   // The stash (Section IV-A step 4) holds keys that found no bucket room.
@@ -904,7 +1009,9 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
 
   // Step 2: claim-then-commit for absent keys.
   bool to_ovf = false;
-  if (kIns && !done && op == OP_INSERT) {
+  if (DEFER && kIns && !done && op == OP_INSERT) {
+    to_ovf = true;  // k_claim places it
+  } else if (kIns && !done && op == OP_INSERT) {
     const uint64_t word = pack(key, val);
     const bool first1 = v.placement ? (f1 > 0) : (f1 >= f2);
     const uint32_t tb = first1 ? b1 : b2, ts = first1 ? s1 : s2;
@@ -930,7 +1037,14 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
   // Hand full-bucket inserts to the eviction kernel (steps 3-4).
   if (kIns) {
     const unsigned om = __ballot_sync(kFull, to_ovf);
-    if (om) {
+    if (DEFER) {
+      if (to_ovf) {
+        const unsigned r = (c << 5) + __popc(om & ((1u << lane) - 1u));
+        ovf.words[r] = pack(key, val);
+        ovf.idx[r] = i;
+      }
+      if (lane == 0) ovf.chunk_cnt[c] = static_cast<uint8_t>(__popc(om));
+    } else if (om) {
       const int leader = __ffs(om) - 1;
       unsigned base = 0;
       if (lane == leader) base = atomicAdd(ovf.count, static_cast<unsigned>(__popc(om)));
@@ -970,7 +1084,7 @@ __global__ void __launch_bounds__(kOpsThreads, staged_mode(MODE, S)
   if (staged_mode(MODE, S)) {
     // bucket reads staged in shared memory
     extern __shared__ __align__(16) uint64_t ops_smem[];
-    Stage sg = stage_init(ops_smem, threadIdx.x >> 5, lane, stage_words(MODE, S));
+    Stage sg = stage_init(ops_smem, threadIdx.x >> 5, lane, warp_smem_words(MODE, S));
     // inputs are loaded one chunk ahead, so their latency hides behind the
     // current chunk's probes and claims
     OpIn nxt{};
@@ -978,14 +1092,107 @@ __global__ void __launch_bounds__(kOpsThreads, staged_mode(MODE, S)
     for (uint32_t c = warp0; c < nchunks; c += nwarps) {
       const OpIn cur = nxt;
       if (c + nwarps < nchunks) nxt = load_in<MODE>(a, c + nwarps, n, lane);
-      run_chunk<MODE, S>(v, stash_n, a, c, n, ovf, 0, cnt, lane, &sg, &cur);
+      run_chunk<MODE, S, MODE == kModeMixed>(v, stash_n, a, c, n, ovf, 0, cnt, lane, &sg, &cur);
     }
     stage_drain(sg);
+    // the staging buffers are free now (a dead stage's late copies have landed
+    // or stage_drain gave up on them, and then its first words stay unused)
+    if (!__syncthreads_or(sg.dead ? 1 : 0))
+      flush_counters_block(v, cnt, lane, sg.buf, ops_smem + 2, warp_smem_words(MODE, S));
+    else
+      flush_counters(v, cnt, lane);
   } else {
     for (uint32_t c = warp0; c < nchunks; c += nwarps)
-      run_chunk<MODE, S>(v, stash_n, a, c, n, ovf, 0, cnt, lane);
+      run_chunk<MODE, S, MODE == kModeMixed>(v, stash_n, a, c, n, ovf, 0, cnt, lane);
+    flush_counters(v, cnt, lane);
   }
-  flush_counters(v, cnt, lane);
+}
+
+// Step 2 for the new keys of a mixed batch (WABC, Section III-E), after the
+// bulk kernel has run every find, erase and replace of the batch: the slots
+// those erases freed are then visible to the claims.  The bulk kernel left
+// chunk c's new keys at list places [32c, 32c + chunk_cnt[c]).  A warp takes 32
+// chunks at a time, scans their counts and spreads their entries over its
+// lanes, one item per lane: hash, read both free masks, claim the predicted
+// slot of the emptier bucket with one atomicAnd (the other bucket next),
+// store the word.  Nothing moves or erases a word meanwhile, so the claim
+// publishes with a plain store.  Items whose two buckets are both full go to
+// `out` for eviction (steps 3-4).
+constexpr int kClaimThreads = 256;
+template <int S>
+__global__ void __launch_bounds__(kClaimThreads)
+    k_claim(View v, List in, uint32_t nchunks, List out, uint8_t* __restrict__ status) {
+  __shared__ __align__(16) uint64_t claim_smem[(kClaimThreads / 32) * kOvfBufWords];
+  const int lane = threadIdx.x & 31;
+  OvfBuf ob = ovf_buf_init(claim_smem + (threadIdx.x >> 5) * kOvfBufWords);
+  LaneCounters cnt;
+  const uint32_t ngroups = (nchunks + 31) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroups; g += nwarps) {
+    const uint32_t c = (g << 5) + lane;
+    const uint32_t k = c < nchunks ? in.chunk_cnt[c] : 0u;
+    uint32_t incl = k;  // inclusive prefix sum of the 32 counts
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += t;
+    }
+    const uint32_t excl = incl - k;
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+      const uint32_t t = t0 + lane;
+      const bool valid = t < total;
+      // chunk j of entry t: the first j whose inclusive sum passes t
+      uint32_t j = 0;
+#pragma unroll
+      for (uint32_t step = 16; step; step >>= 1) {
+        const uint32_t e = __shfl_sync(kFull, incl, j + step - 1);
+        if (e <= t) j += step;
+      }
+      const uint32_t ex = __shfl_sync(kFull, excl, j & 31);
+      const uint32_t pos = (((g << 5) + j) << 5) + (t - ex);
+      const uint64_t word = valid ? in.words[pos] : kEmptyWord;
+      const uint32_t idx = valid ? in.idx[pos] : kNoOp;
+      bool to_ovf = false;
+      if (valid) {
+        const uint32_t key = key_of(word);
+        const uint32_t b1 = lh_bucket(bithash1(key), v.M, v.p);
+        const uint32_t b2 = lh_bucket(bithash2(key), v.M, v.p);
+        const uint32_t m1 = ld_relaxed32(v.masks + b1);
+        const uint32_t m2 = ld_relaxed32(v.masks + b2);
+        const uint32_t f1 = __popc(m1), f2 = __popc(m2);
+        const bool first1 = v.placement ? (f1 > 0) : (f1 >= f2);
+        const uint32_t tb = first1 ? b1 : b2, xb = first1 ? b2 : b1;
+        const uint32_t tm = first1 ? m1 : m2, xm = first1 ? m2 : m1;
+        bool placed = false;
+        if (f1 + f2 > 0) {
+          placed = claim_store<S>(v, tb, tm ? __ffs(tm) - 1 : S, word);
+          if (!placed && xb != tb) placed = claim_store<S>(v, xb, xm ? __ffs(xm) - 1 : S, word);
+        }
+        if (placed) {
+          cnt.size_delta += 1;
+          cnt.claimed += 1;
+          if (status && idx != kNoOp) status[idx] = ST_INSERTED;
+        } else {
+          to_ovf = true;
+          cnt.overflowed += 1;
+        }
+      }
+      const unsigned om = __ballot_sync(kFull, to_ovf);
+      if (om) {
+        if (ob.n + __popc(om) > kOvfBuf) ovf_flush(out, ob, lane);
+        if (to_ovf) {
+          const unsigned r = ob.n + __popc(om & ((1u << lane) - 1u));
+          ob.words[r] = word;
+          ob.idx[r] = idx;
+          ob.seg[r] = 0;
+        }
+        ob.n += __popc(om);
+      }
+    }
+  }
+  ovf_flush(out, ob, lane);
+  flush_counters_block(v, cnt, lane, ob.words, claim_smem, kOvfBufWords);
 }
 
 // ----------------------------------------------------------------------------
@@ -1973,6 +2180,21 @@ cudaError_t launch_ops(int mode, const View& v, const uint8_t* ops, const uint32
   return launch_ops_s<32>(mode, v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
 }
 
+cudaError_t launch_claim(const View& v, List in, uint64_t n, List out, uint8_t* status,
+                         const Launch& L, cudaStream_t s) {
+  if (!n) return cudaSuccess;
+  const uint32_t nchunks = static_cast<uint32_t>((n + 31) / 32);
+  uint64_t blocks = ((nchunks + 31) / 32 + kClaimThreads / 32 - 1) / (kClaimThreads / 32);
+  const uint64_t cap = static_cast<uint64_t>(L.num_sms) * L.claim_blocks_per_sm;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  if (v.S == 16)
+    k_claim<16><<<static_cast<unsigned>(blocks), kClaimThreads, 0, s>>>(v, in, nchunks, out, status);
+  else
+    k_claim<32><<<static_cast<unsigned>(blocks), kClaimThreads, 0, s>>>(v, in, nchunks, out, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_overflow(const View& v, List in, List pend, int resizable, uint8_t* status,
                             const Launch& L, cudaStream_t s) {
   const unsigned blocks = static_cast<unsigned>(L.num_sms * L.ovf_blocks_per_sm);
@@ -2125,6 +2347,9 @@ cudaError_t occupancy_s(Launch* L) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_overflow<S>, kOvfThreads, 0);
   if (e != cudaSuccess) return e;
   L->ovf_blocks_per_sm = b > 0 ? b : 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_claim<S>, kClaimThreads, 0);
+  if (e != cudaSuccess) return e;
+  L->claim_blocks_per_sm = b > 0 ? b : 1;
   const int smem = static_cast<int>(kMaintSmemWords * sizeof(uint64_t));
   e = cudaFuncSetAttribute(k_multi_maint<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

@@ -38,7 +38,7 @@ EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", 
            "hive32_check",
            "hive32_stats", "hive32_dump"]
 KERNEL_KINDS = ["find", "insert", "erase", "mixed", "evict", "maint", "split", "merge", "count",
-                "fused"]
+                "fused", "claim"]
 
 
 class HiveError(RuntimeError):
