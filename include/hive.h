@@ -102,6 +102,19 @@ typedef struct {
                                capacity, see hive_memory); 0 = allocate max_slots
                                of buckets up front (default; faster on the
                                multi-table path) */
+  uint32_t l2_persist;      /* 1 = the kernels that claim slots (bulk insert,
+                               mixed batch, claims, eviction) keep the free masks
+                               in a persisting L2 access-policy window, so that
+                               the claim atomics hit L2 while the bucket reads
+                               stream past; the first such table of the process
+                               sets the CUDA context's persisting-L2 limit (a
+                               per-process setting, gone when the process exits).
+                               0 = off (default; a tuning knob) */
+  uint32_t stage_wait_limit;/* tries before a wait for staged bucket copies
+                               gives up (TIMEOUT) and the round is redone with
+                               direct loads; 0 = 2^22 (default).  Only the
+                               256-byte-bucket (S = 32) copies wait on an
+                               mbarrier; a small value exercises the fallback */
 } hive_config;
 
 /* Per-table counters, accumulated since creation or the last hive_clear.
@@ -109,7 +122,8 @@ typedef struct {
  * step 3 bounded cuckoo eviction, step 4 overflow stash. */
 typedef struct {
   uint64_t replaced;         /* inserts finished in step 1 */
-  uint64_t claimed_fast;     /* inserts finished in step 2 by the bulk kernel */
+  uint64_t claimed_fast;     /* inserts finished in step 2 by the bulk kernel
+                                (mixed batches: by the claim kernel that follows it) */
   uint64_t overflowed;       /* inserts handed to the eviction kernel */
   uint64_t claimed_slow;     /* of those, placed by a lock-free claim */
   uint64_t evict_rounds;     /* displacement rounds executed (step 3) */

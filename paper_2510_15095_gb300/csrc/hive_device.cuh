@@ -141,6 +141,24 @@ __device__ __forceinline__ void cp_async_commit() {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
+// Asks L2 to fetch [p, p + bytes) from memory (bytes a multiple of 16, p
+// 16-byte aligned); nothing waits for it.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+// Spreads a bulk L2 prefetch of [base, base + bytes) over the blocks of a
+// grid, 64 KB per instruction, issued by one thread of each block.
+__device__ __forceinline__ void prefetch_l2_grid(const void* base, uint64_t bytes) {
+  if (threadIdx.x != 0) return;
+  constexpr uint64_t kPiece = 64 * 1024;
+  const char* b = static_cast<const char*>(base);
+  bytes &= ~static_cast<uint64_t>(15);
+  for (uint64_t off = static_cast<uint64_t>(blockIdx.x) * kPiece; off < bytes;
+       off += static_cast<uint64_t>(gridDim.x) * kPiece) {
+    const uint64_t len = bytes - off < kPiece ? bytes - off : kPiece;
+    prefetch_l2_bulk(b + off, static_cast<uint32_t>(len));
+  }
+}
 __device__ __forceinline__ uint32_t ld_acquire32(const uint32_t* p) {
   uint32_t r;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");

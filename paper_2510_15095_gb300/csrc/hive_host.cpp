@@ -113,6 +113,7 @@ View hive::make_view(const hive_table* t) {
   v.lock_spin_limit = t->cfg.lock_spin_limit;
   v.placement = t->cfg.placement;
   v.S = t->S;
+  v.stage_spin_limit = t->cfg.stage_wait_limit ? t->cfg.stage_wait_limit : (1u << 22);
   return v;
 }
 
@@ -439,6 +440,33 @@ void hive_config_default(hive_config* cfg) {
   cfg->lock_spin_limit = 1u << 14;
 }
 
+// The persisting L2 window of a table's free masks (hive_config.l2_persist):
+// as many mask bytes as one window may cover, and a persisting set-aside of
+// the context at least that large (never lowered, capped at the device's
+// maximum).  With a set-aside smaller than the window, the hit ratio scales
+// down so that the persisting lines fit.
+static cudaError_t setup_l2_window(hive_table* t) {
+  int max_win = 0, max_persist = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, t->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, t->device);
+  if (e != cudaSuccess) return e;
+  if (max_win <= 0 || max_persist <= 0) return cudaSuccess;  // no persisting L2 here
+  const size_t bytes = std::min<size_t>(t->nb_max * sizeof(uint32_t), static_cast<size_t>(max_win));
+  size_t cur = 0;
+  if ((e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize)) != cudaSuccess) return e;
+  if (cur < bytes) {
+    const size_t want = std::min<size_t>(bytes, static_cast<size_t>(max_persist));
+    if ((e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize)) != cudaSuccess) return e;
+  }
+  if (cur == 0) return cudaSuccess;
+  t->L.l2_base = t->masks;
+  t->L.l2_bytes = bytes;
+  t->L.l2_hit = cur >= bytes ? 1.0f : static_cast<float>(cur) / static_cast<float>(bytes);
+  return cudaSuccess;
+}
+
 hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) {
   if (!cfg || !out) return fail(HIVE_ERR_INVALID_ARG, "cfg and out must not be NULL");
   *out = nullptr;
@@ -452,9 +480,11 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
           static_cast<uint64_t>(cfg->grow_num) * cfg->shrink_den)
     return fail(HIVE_ERR_INVALID_ARG, "need 0 <= shrink < grow <= 1");
   if (cfg->stash_permille > 1000 || cfg->placement > HIVE_PLACE_FIRST || cfg->blocks_per_sm > 64 ||
-      cfg->map_on_demand > 1 ||
+      cfg->map_on_demand > 1 || cfg->l2_persist > 1 ||
       cfg->resizable > 1)
-    return fail(HIVE_ERR_INVALID_ARG, "bad stash_permille, placement, resizable or blocks_per_sm");
+    return fail(HIVE_ERR_INVALID_ARG,
+                "bad stash_permille, placement, resizable, blocks_per_sm, map_on_demand or "
+                "l2_persist");
 
   hive_table* t = new (std::nothrow) hive_table();
   if (!t) return fail(HIVE_ERR_OOM, "host allocation failed");
@@ -517,6 +547,7 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
   if (e == cudaSuccess) e = cudaMemsetAsync(t->locks, 0, 2 * t->nb_max * sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->stash_kv, 0xFF, t->stash_alloc * sizeof(uint64_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->ctrl, 0, sizeof(Ctrl), s);
+  if (e == cudaSuccess && cfg->l2_persist) e = setup_l2_window(t);
   if (e != cudaSuccess) {
     hive_status st = cuda_fail(e, "hive_create");
     hive_destroy(t);
@@ -611,6 +642,13 @@ hive_status hive_erase(hive_table* t, const uint32_t* keys, uint64_t n, uint8_t*
   return HIVE_OK;
 }
 
+// Mixed batches of at least this many ops claim their new keys in a second
+// kernel (launch_claim) after every find, erase and replace: at high load the
+// slots the batch's erases free then take most of the keys whose buckets
+// were full when probed.  Smaller batches claim in the bulk kernel and save
+// the launch.
+constexpr uint64_t kDeferMin = 1u << 18;
+
 hive_status hive_execute(hive_table* t, const uint8_t* ops, const uint32_t* keys,
                          const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* status,
                          void* stream) {
@@ -631,19 +669,31 @@ hive_status hive_execute(hive_table* t, const uint8_t* ops, const uint32_t* keys
     if ((st = grow_for(t, t->host_ctrl->n_insert, s)) != HIVE_OK) return st;
   }
   const View v = make_view(t);
-  // P1: finds, erases and replaces; the new keys are listed in A (reading 14:
-  // no op of P1 moves a word, and the claims of P2 see every slot P1 freed)
+  // Both op lists are empty here: every mutating call ends with the
+  // maintenance kernel, which resets their counts.
+  if (n < kDeferMin) {
+    // P1 with the claims of new keys, then eviction and stash for the keys
+    // whose buckets were both full
+    HIVE_LAUNCH(t, HIVE_K_MIXED, s,
+                launch_ops(kModeMixed, v, ops, keys, vals, n, vals_out, nullptr, status,
+                           list_a(t), t->L, s));
+    HIVE_LAUNCH(t, HIVE_K_EVICT, s,
+                launch_overflow(v, list_a(t), list_b(t), t->cfg.resizable, status, t->L, s));
+    if (t->cfg.resizable) return finish_resizable(t, status, s);
+    HIVE_LAUNCH(t, HIVE_K_MAINT, s, launch_maintenance(v, s));
+    return HIVE_OK;
+  }
+  // P1: finds, erases and replaces; the new keys wait in A chunk by chunk
+  // (reading 14: no op of P1 moves a word, and the claims of P2 then see
+  // every slot that P1's erases freed)
   HIVE_LAUNCH(t, HIVE_K_MIXED, s,
               launch_ops(kModeMixed, v, ops, keys, vals, n, vals_out, nullptr, status,
-                         list_a(t), t->L, s));
-  // P2: claims (A -> B for both-full buckets), then eviction and stash (B,
-  // with pending items back to A)
-  HIVE_CK(cudaMemsetAsync(&t->ctrl->pend_n, 0, sizeof(unsigned), s));
+                         list_a(t), t->L, s, true));
+  // P2: claims (A -> B for keys whose buckets are both full), then eviction
+  // and stash (B, with pending items appended to A, whose count is still 0)
   HIVE_LAUNCH(t, HIVE_K_CLAIM, s, launch_claim(v, list_a(t), n, list_b(t), status, t->L, s));
-  HIVE_CK(cudaMemsetAsync(&t->ctrl->ovf_n, 0, sizeof(unsigned), s));
   HIVE_LAUNCH(t, HIVE_K_EVICT, s,
               launch_overflow(v, list_b(t), list_a(t), t->cfg.resizable, status, t->L, s));
-  HIVE_CK(cudaMemsetAsync(&t->ctrl->pend_n, 0, sizeof(unsigned), s));
   if (t->cfg.resizable) return finish_resizable(t, status, s, false);
   HIVE_LAUNCH(t, HIVE_K_MAINT, s, launch_maintenance(v, s));
   return HIVE_OK;

@@ -79,6 +79,7 @@ struct View {
   uint32_t lock_spin_limit;
   uint32_t placement;    // 0 balanced, 1 BitHash1 first
   uint32_t S;            // slots per bucket: 16 or 32
+  uint32_t stage_spin_limit;  // tries of a staged-copy wait before it gives up
 };
 
 // An op list handed from the bulk kernel to the eviction kernel.
@@ -128,12 +129,20 @@ struct Launch {
   int ovf_blocks_per_sm;
   int multi_blocks_per_sm;
   int claim_blocks_per_sm;   // claims of a mixed batch's new keys
+  // persisting L2 window over the free masks for the kernels that claim
+  // slots (l2_bytes = 0: none)
+  void* l2_base;
+  size_t l2_bytes;
+  float l2_hit;
 };
 
 // Kernel launchers (hive_kernels.cu).  Each returns the launch error.
+// defer (mixed batches): new keys go to list A chunk by chunk for
+// launch_claim instead of claiming in the bulk kernel.
 cudaError_t launch_ops(int mode, const View& v, const uint8_t* ops, const uint32_t* keys,
                        const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
-                       uint8_t* status, List ovf, const Launch& L, cudaStream_t s);
+                       uint8_t* status, List ovf, const Launch& L, cudaStream_t s,
+                       bool defer = false);
 cudaError_t launch_overflow(const View& v, List in, List pend, int resizable, uint8_t* status,
                             const Launch& L, cudaStream_t s);
 // Claims for the new keys of a mixed batch of n ops, left in `in` chunk by

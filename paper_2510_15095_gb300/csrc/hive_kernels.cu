@@ -63,6 +63,12 @@ constexpr int kOpsThreads = 256;
 #ifndef HIVE_STAGE_LSU_S32
 #define HIVE_STAGE_LSU_S32 0
 #endif
+// Where the paired insert round takes the free slots that steer its claims:
+// 1 = the EMPTY words of the staged buckets (no mask reads), 0 = the two
+// free masks, read while the copies are in flight.
+#ifndef HIVE_FREE_FROM_STAGE
+#define HIVE_FREE_FROM_STAGE 1
+#endif
 #ifndef HIVE_STAGED_SMALL_MIN_BLOCKS
 #define HIVE_STAGED_SMALL_MIN_BLOCKS 4  // 32 KB of staging per block (S = 16 single rounds)
 #endif
@@ -236,8 +242,9 @@ struct Geo {
 // path (stage_issue_lsu); 256-byte buckets with one bulk copy (TMA) each,
 // counted by the barrier (stage_issue).  Each lane then scans its own op's
 // buckets in shared memory.  A barrier wait that does not end within
-// kMbarSpinLimit tries raises the table's sticky TIMEOUT error, marks the
-// stage dead and redoes the round from global memory.
+// View::stage_spin_limit tries raises the table's sticky TIMEOUT error, marks
+// the stage dead and redoes the round from global memory; before the warp
+// exits it waits up to kMbarSpinLimit tries for the copies still in flight.
 constexpr int kStageWords = 1024;
 constexpr uint32_t kMbarSpinLimit = 1u << 22;
 
@@ -326,7 +333,7 @@ __device__ __forceinline__ void stage_issue(const View& v, Stage& sg, unsigned n
 // Waits (bounded, warp-wide) for the copies of the round issued last.
 __device__ __forceinline__ bool stage_wait(const View& v, Stage& sg, int lane) {
   bool ok = false;
-  for (uint32_t it = 0; it < kMbarSpinLimit && !ok; ++it) ok = mbar_try_wait(sg.bar, sg.phase);
+  for (uint32_t it = 0; it < v.stage_spin_limit && !ok; ++it) ok = mbar_try_wait(sg.bar, sg.phase);
   sg.phase ^= 1u;
   if (__any_sync(kFull, !ok)) {  // never expected
     sg.dead = true;
@@ -365,16 +372,31 @@ __device__ __forceinline__ void stage_wait_lsu() {
   __syncwarp();
 }
 
+// A staged round in two halves, so that a caller can do other work while the
+// copies are in flight: stage_begin() issues them on the path chosen for the
+// bucket width, stage_end() waits (false: the wait gave up, see stage_wait).
 template <int S, bool PAIR>
-__device__ __forceinline__ bool stage_round(const View& v, Stage& sg, unsigned need, int o0,
+__device__ __forceinline__ void stage_begin(const View& v, Stage& sg, unsigned need, int o0,
                                             uint32_t x1, uint32_t x2, int lane) {
-  if (S == 16 ? HIVE_STAGE_LSU_S16 : HIVE_STAGE_LSU_S32) {
+  if (S == 16 ? HIVE_STAGE_LSU_S16 : HIVE_STAGE_LSU_S32)
     stage_issue_lsu<S, PAIR>(v, sg, need, o0, x1, x2, lane);
+  else
+    stage_issue<S, PAIR>(v, sg, need, o0, x1, x2, lane);
+}
+template <int S>
+__device__ __forceinline__ bool stage_end(const View& v, Stage& sg, int lane) {
+  if (S == 16 ? HIVE_STAGE_LSU_S16 : HIVE_STAGE_LSU_S32) {
     stage_wait_lsu();
     return true;
   }
-  stage_issue<S, PAIR>(v, sg, need, o0, x1, x2, lane);
   return stage_wait(v, sg, lane);
+}
+
+template <int S, bool PAIR>
+__device__ __forceinline__ bool stage_round(const View& v, Stage& sg, unsigned need, int o0,
+                                            uint32_t x1, uint32_t x2, int lane) {
+  stage_begin<S, PAIR>(v, sg, need, o0, x1, x2, lane);
+  return stage_end<S>(v, sg, lane);
 }
 
 // One probe round over the 32 ops of a warp.  `need` has bit j set when op j
@@ -707,8 +729,10 @@ __device__ __forceinline__ void probe_round(const View& v, unsigned need, uint32
 // so that the eight lanes of a shared-memory wavefront read eight different
 // bank groups, and one compare per slot against the op's key (a key sits in
 // at most one slot of the table).  Free counts and first free slots come from
-// the free masks, read from global memory while the copies are in flight:
-// they only steer the claim, whose fetch_and result is the authority.  This
+// the EMPTY words of the staged buckets (HIVE_FREE_FROM_STAGE), or from the
+// free masks read while the copies are in flight: either way they only steer
+// the claim, whose fetch_and result is the authority (a slot claimed and not
+// yet written still reads EMPTY; the claim then retries on the returned mask).  This
 // takes a few instructions per slot where the warp-wide match-and-elect takes
 // several ballots per 16-byte fragment, and the staged kernel is bound by
 // instruction issue, not by memory.
@@ -722,6 +746,7 @@ __device__ __forceinline__ void scan_staged_pair(const View& v, const uint64_t* 
   constexpr int NP = S / 2;  // 16-byte fragments per bucket
   const uint64_t* B = sbuf + 2 * jj * S;
   int ms = -1;  // matched word in [0, 2S): bucket ms / S, slot ms % S
+  uint32_t em[2] = {0u, 0u};  // EMPTY slots of each bucket
 #pragma unroll
   for (int which = 0; which < 2; ++which) {
 #pragma unroll 8
@@ -731,7 +756,14 @@ __device__ __forceinline__ void scan_staged_pair(const View& v, const uint64_t* 
       lds_frag(B + which * S + 2 * f, a, b);
       if (key_of(a) == key) ms = which * S + 2 * f;
       if (key_of(b) == key) ms = which * S + 2 * f + 1;
+      if (HIVE_FREE_FROM_STAGE)
+        em[which] |= ((key_of(a) == kEmptyKey ? 1u : 0u) | (key_of(b) == kEmptyKey ? 2u : 0u))
+                     << (2 * f);
     }
+  }
+  if (HIVE_FREE_FROM_STAGE) {
+    m1 = em[0];
+    m2 = em[1];
   }
   if (ms >= 0) {
     done = true;
@@ -762,8 +794,9 @@ __device__ __forceinline__ void probe_pair_round(const View& v, unsigned need, u
   constexpr int BO = kStageWords / (2 * S);
   constexpr unsigned BM = (BO >= 32) ? 0xFFFFFFFFu : ((1u << BO) - 1u);
   if (sg) {
-    // free masks of both buckets, in flight beside the copies
-    const bool mine = (need >> lane) & 1u;
+    // free masks of both buckets, in flight beside the copies (unless the
+    // staged words give the free slots)
+    const bool mine = !HIVE_FREE_FROM_STAGE && ((need >> lane) & 1u);
     const uint32_t m1 = mine ? ld_relaxed32(v.masks + b1) : 0u;
     const uint32_t m2 = mine ? ld_relaxed32(v.masks + b2) : 0u;
 #pragma unroll 1
@@ -897,21 +930,23 @@ __device__ __forceinline__ OpIn load_in(const OpPtrs& a, uint32_t c, uint64_t n,
 // queued behind each other in L2 and held up every warp's memory pipeline.
 // (The bulk kernel's own eviction hand-off is rare enough to append directly;
 // a mixed batch's new keys go to fixed per-chunk places, see run_chunk.)
-constexpr int kOvfBuf = 32;
-constexpr int kOvfBufWords = kOvfBuf + kOvfBuf / 2 + kOvfBuf / 2;
+// A buffer of `cap` entries takes 2 * cap shared-memory words: cap packed
+// words, then cap op indices and cap segment tags (u32).
 struct OvfBuf {
-  uint64_t* words;  // kOvfBuf entries each
+  uint64_t* words;
   uint32_t* idx;
   uint32_t* seg;
   uint32_t n;       // entries held (warp-uniform)
+  uint32_t cap;
 };
 
-__device__ __forceinline__ OvfBuf ovf_buf_init(uint64_t* region) {
+__device__ __forceinline__ OvfBuf ovf_buf_init(uint64_t* region, uint32_t cap) {
   OvfBuf ob;
   ob.words = region;
-  ob.idx = reinterpret_cast<uint32_t*>(region + kOvfBuf);
-  ob.seg = ob.idx + kOvfBuf;
+  ob.idx = reinterpret_cast<uint32_t*>(region + cap);
+  ob.seg = ob.idx + cap;
   ob.n = 0;
+  ob.cap = cap;
   return ob;
 }
 
@@ -922,6 +957,47 @@ __device__ __forceinline__ void ovf_flush(const List& ovf, OvfBuf& ob, int lane)
   unsigned base = 0;
   if (lane == 0) base = atomicAdd(ovf.count, ob.n);
   base = __shfl_sync(kFull, base, 0);
+  for (uint32_t j = lane; j < ob.n; j += 32) {
+    ovf.words[base + j] = ob.words[j];
+    ovf.idx[base + j] = ob.idx[j];
+    if (ovf.seg) ovf.seg[base + j] = ob.seg[j];
+  }
+  __syncwarp();
+  ob.n = 0;
+}
+
+// Adds one round's entries (lanes with `put`) to the buffer, flushing first
+// if they would not fit.
+__device__ __forceinline__ void ovf_put(const List& ovf, OvfBuf& ob, int lane, bool put,
+                                        uint64_t word, uint32_t idx, uint32_t seg) {
+  const unsigned om = __ballot_sync(kFull, put);
+  if (!om) return;
+  if (ob.n + __popc(om) > ob.cap) ovf_flush(ovf, ob, lane);
+  if (put) {
+    const unsigned r = ob.n + __popc(om & ((1u << lane) - 1u));
+    ob.words[r] = word;
+    ob.idx[r] = idx;
+    ob.seg[r] = seg;
+  }
+  ob.n += __popc(om);
+}
+
+// The final flush of every warp of a block at once: one atomicAdd reserves
+// the list space of the whole block.  Every thread of the block calls it.
+__device__ __forceinline__ void ovf_flush_block(const List& ovf, OvfBuf& ob, int lane) {
+  __shared__ unsigned warp_n[32];
+  __shared__ unsigned block_base;
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) warp_n[w] = ob.n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned tot = 0;
+    for (int k = 0; k < nw; ++k) tot += warp_n[k];
+    block_base = tot ? atomicAdd(ovf.count, tot) : 0u;
+  }
+  __syncthreads();
+  unsigned base = block_base;
+  for (int k = 0; k < w; ++k) base += warp_n[k];
   for (uint32_t j = lane; j < ob.n; j += 32) {
     ovf.words[base + j] = ob.words[j];
     ovf.idx[base + j] = ob.idx[j];
@@ -1069,11 +1145,15 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
   }
 }
 
-template <int MODE, int S>
+// DEFER (mixed batches): the new keys are claimed by k_claim afterwards.
+template <int MODE, int S, bool DEFER>
 __global__ void __launch_bounds__(kOpsThreads, staged_mode(MODE, S)
                                                    ? staged_min_blocks(MODE, S)
                                                    : HIVE_OPS_MIN_BLOCKS)
-    k_ops(View v, OpPtrs a, uint64_t n, List ovf) {
+    k_ops(View v, OpPtrs a, uint64_t n, List ovf, int prefetch_masks) {
+  // claims and erases update free masks at random; a large batch first asks
+  // L2 for the whole mask array in sequential pieces
+  if (prefetch_masks) prefetch_l2_grid(v.masks, static_cast<uint64_t>(v.nb) * sizeof(uint32_t));
   const int lane = threadIdx.x & 31;
   // n < 2^32 per call, so chunk and op indices fit 32 bits
   const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1092,7 +1172,7 @@ __global__ void __launch_bounds__(kOpsThreads, staged_mode(MODE, S)
     for (uint32_t c = warp0; c < nchunks; c += nwarps) {
       const OpIn cur = nxt;
       if (c + nwarps < nchunks) nxt = load_in<MODE>(a, c + nwarps, n, lane);
-      run_chunk<MODE, S, MODE == kModeMixed>(v, stash_n, a, c, n, ovf, 0, cnt, lane, &sg, &cur);
+      run_chunk<MODE, S, DEFER>(v, stash_n, a, c, n, ovf, 0, cnt, lane, &sg, &cur);
     }
     stage_drain(sg);
     // the staging buffers are free now (a dead stage's late copies have landed
@@ -1103,7 +1183,7 @@ __global__ void __launch_bounds__(kOpsThreads, staged_mode(MODE, S)
       flush_counters(v, cnt, lane);
   } else {
     for (uint32_t c = warp0; c < nchunks; c += nwarps)
-      run_chunk<MODE, S, MODE == kModeMixed>(v, stash_n, a, c, n, ovf, 0, cnt, lane);
+      run_chunk<MODE, S, DEFER>(v, stash_n, a, c, n, ovf, 0, cnt, lane);
     flush_counters(v, cnt, lane);
   }
 }
@@ -1119,18 +1199,35 @@ __global__ void __launch_bounds__(kOpsThreads, staged_mode(MODE, S)
 // publishes with a plain store.  Items whose two buckets are both full go to
 // `out` for eviction (steps 3-4).
 constexpr int kClaimThreads = 256;
+constexpr int kClaimBuf = 256;  // entries of each warp's buffer of full-bucket items
+#ifndef HIVE_CLAIM_PREFETCH_SLOT
+#define HIVE_CLAIM_PREFETCH_SLOT 0
+#endif
+#ifndef HIVE_CLAIM_ILP
+#define HIVE_CLAIM_ILP 4
+#endif
+constexpr int kClaimIlp = HIVE_CLAIM_ILP;  // items per lane in flight at once
 template <int S>
 __global__ void __launch_bounds__(kClaimThreads)
-    k_claim(View v, List in, uint32_t nchunks, List out, uint8_t* __restrict__ status) {
-  __shared__ __align__(16) uint64_t claim_smem[(kClaimThreads / 32) * kOvfBufWords];
+    k_claim(View v, List in, uint32_t nchunks, List out, uint8_t* __restrict__ status,
+            int prefetch_masks) {
+  // The claims read the free masks at random: a batch with as many new keys
+  // as a fraction of the buckets is served faster from L2 after one
+  // sequential fetch of the whole mask array than by a DRAM sector per read.
+  if (prefetch_masks) prefetch_l2_grid(v.masks, static_cast<uint64_t>(v.nb) * sizeof(uint32_t));
+  __shared__ __align__(16) uint64_t claim_smem[(kClaimThreads / 32) * 2 * kClaimBuf];
   const int lane = threadIdx.x & 31;
-  OvfBuf ob = ovf_buf_init(claim_smem + (threadIdx.x >> 5) * kOvfBufWords);
+  OvfBuf ob = ovf_buf_init(claim_smem + (threadIdx.x >> 5) * 2 * kClaimBuf, kClaimBuf);
   LaneCounters cnt;
   const uint32_t ngroups = (nchunks + 31) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroups; g += nwarps) {
-    const uint32_t c = (g << 5) + lane;
-    const uint32_t k = c < nchunks ? in.chunk_cnt[c] : 0u;
+  uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // chunk counts are loaded one group ahead
+  uint32_t k_next = (g < ngroups && (g << 5) + lane < nchunks) ? in.chunk_cnt[(g << 5) + lane] : 0u;
+  for (; g < ngroups; g += nwarps) {
+    const uint32_t k = k_next;
+    const uint32_t gn = g + nwarps;
+    k_next = (gn < ngroups && (gn << 5) + lane < nchunks) ? in.chunk_cnt[(gn << 5) + lane] : 0u;
     uint32_t incl = k;  // inclusive prefix sum of the 32 counts
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -1139,60 +1236,84 @@ __global__ void __launch_bounds__(kClaimThreads)
     }
     const uint32_t excl = incl - k;
     const uint32_t total = __shfl_sync(kFull, incl, 31);
-    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
-      const uint32_t t = t0 + lane;
-      const bool valid = t < total;
-      // chunk j of entry t: the first j whose inclusive sum passes t
-      uint32_t j = 0;
+    for (uint32_t t0 = 0; t0 < total; t0 += 32 * kClaimIlp) {
+      uint64_t word[kClaimIlp];
+      uint32_t idx[kClaimIlp], b1[kClaimIlp], b2[kClaimIlp], m1[kClaimIlp], m2[kClaimIlp];
 #pragma unroll
-      for (uint32_t step = 16; step; step >>= 1) {
-        const uint32_t e = __shfl_sync(kFull, incl, j + step - 1);
-        if (e <= t) j += step;
+      for (int u = 0; u < kClaimIlp; ++u) {
+        const uint32_t t = t0 + 32 * u + lane;
+        // chunk j of entry t: the first j whose inclusive sum passes t
+        uint32_t j = 0;
+#pragma unroll
+        for (uint32_t step = 16; step; step >>= 1) {
+          const uint32_t e = __shfl_sync(kFull, incl, j + step - 1);
+          if (e <= t) j += step;
+        }
+        const uint32_t ex = __shfl_sync(kFull, excl, j & 31);
+        const uint32_t pos = (((g << 5) + j) << 5) + (t - ex);
+        word[u] = t < total ? in.words[pos] : kEmptyWord;
+        idx[u] = t < total ? in.idx[pos] : kNoOp;
       }
-      const uint32_t ex = __shfl_sync(kFull, excl, j & 31);
-      const uint32_t pos = (((g << 5) + j) << 5) + (t - ex);
-      const uint64_t word = valid ? in.words[pos] : kEmptyWord;
-      const uint32_t idx = valid ? in.idx[pos] : kNoOp;
-      bool to_ovf = false;
-      if (valid) {
-        const uint32_t key = key_of(word);
-        const uint32_t b1 = lh_bucket(bithash1(key), v.M, v.p);
-        const uint32_t b2 = lh_bucket(bithash2(key), v.M, v.p);
-        const uint32_t m1 = ld_relaxed32(v.masks + b1);
-        const uint32_t m2 = ld_relaxed32(v.masks + b2);
-        const uint32_t f1 = __popc(m1), f2 = __popc(m2);
+#pragma unroll
+      for (int u = 0; u < kClaimIlp; ++u) {
+        const uint32_t key = key_of(word[u]);
+        b1[u] = lh_bucket(bithash1(key), v.M, v.p);
+        b2[u] = lh_bucket(bithash2(key), v.M, v.p);
+        const bool valid = t0 + 32 * u + lane < total;
+        m1[u] = valid ? ld_relaxed32(v.masks + b1[u]) : 0u;
+        m2[u] = valid ? ld_relaxed32(v.masks + b2[u]) : 0u;
+      }
+      // first claim attempt of every item, then the outcomes (a failed
+      // attempt retries on the returned mask, then on the other bucket)
+      uint32_t old[kClaimIlp], bit[kClaimIlp];
+#pragma unroll
+      for (int u = 0; u < kClaimIlp; ++u) {
+        const uint32_t f1 = __popc(m1[u]), f2 = __popc(m2[u]);
         const bool first1 = v.placement ? (f1 > 0) : (f1 >= f2);
-        const uint32_t tb = first1 ? b1 : b2, xb = first1 ? b2 : b1;
-        const uint32_t tm = first1 ? m1 : m2, xm = first1 ? m2 : m1;
-        bool placed = false;
-        if (f1 + f2 > 0) {
-          placed = claim_store<S>(v, tb, tm ? __ffs(tm) - 1 : S, word);
-          if (!placed && xb != tb) placed = claim_store<S>(v, xb, xm ? __ffs(xm) - 1 : S, word);
+        if (!first1) {
+          const uint32_t tb = b1[u], tm = m1[u];
+          b1[u] = b2[u];
+          m1[u] = m2[u];
+          b2[u] = tb;
+          m2[u] = tm;
         }
-        if (placed) {
-          cnt.size_delta += 1;
-          cnt.claimed += 1;
-          if (status && idx != kNoOp) status[idx] = ST_INSERTED;
-        } else {
-          to_ovf = true;
-          cnt.overflowed += 1;
-        }
+        bit[u] = m1[u] ? (1u << (__ffs(m1[u]) - 1)) : 0u;
+#if HIVE_CLAIM_PREFETCH_SLOT
+        if (bit[u])
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(v.buckets + static_cast<uint64_t>(b1[u]) * S +
+                                                          (__ffs(bit[u]) - 1)));
+#endif
+        old[u] = bit[u] ? atomicAnd(v.masks + b1[u], ~bit[u]) : 0u;
       }
-      const unsigned om = __ballot_sync(kFull, to_ovf);
-      if (om) {
-        if (ob.n + __popc(om) > kOvfBuf) ovf_flush(out, ob, lane);
-        if (to_ovf) {
-          const unsigned r = ob.n + __popc(om & ((1u << lane) - 1u));
-          ob.words[r] = word;
-          ob.idx[r] = idx;
-          ob.seg[r] = 0;
+#pragma unroll
+      for (int u = 0; u < kClaimIlp; ++u) {
+        const bool valid = t0 + 32 * u + lane < total;
+        bool placed = false, to_ovf = false;
+        if (valid) {
+          if (old[u] & bit[u]) {
+            st_relaxed64(v.buckets + static_cast<uint64_t>(b1[u]) * S + (__ffs(bit[u]) - 1),
+                         word[u]);
+            placed = true;
+          } else {
+            if (bit[u]) placed = claim_store<S>(v, b1[u], old[u] ? __ffs(old[u]) - 1 : S, word[u]);
+            if (!placed && b2[u] != b1[u] && m2[u])
+              placed = claim_store<S>(v, b2[u], __ffs(m2[u]) - 1, word[u]);
+          }
+          if (placed) {
+            cnt.size_delta += 1;
+            cnt.claimed += 1;
+            if (status && idx[u] != kNoOp) status[idx[u]] = ST_INSERTED;
+          } else {
+            to_ovf = true;
+            cnt.overflowed += 1;
+          }
         }
-        ob.n += __popc(om);
+        ovf_put(out, ob, lane, to_ovf, word[u], idx[u], 0);
       }
     }
   }
-  ovf_flush(out, ob, lane);
-  flush_counters_block(v, cnt, lane, ob.words, claim_smem, kOvfBufWords);
+  ovf_flush_block(out, ob, lane);
+  flush_counters_block(v, cnt, lane, ob.words, claim_smem, 2 * kClaimBuf);
 }
 
 // ----------------------------------------------------------------------------
@@ -1814,7 +1935,10 @@ __device__ void maint_body(const View& v, uint64_t* smem) {
     s_live = 0;
   }
   __syncthreads();
-  if (threadIdx.x == 0) c->ovf_n = 0;  // the next call's overflow list starts empty
+  if (threadIdx.x == 0) {  // the next call's op lists start empty
+    c->ovf_n = 0;
+    c->pend_n = 0;
+  }
   if (tail == sorted && !dirty) return;
 
   // Move stash words back into a candidate bucket that has room.
@@ -2118,7 +2242,32 @@ __global__ void k_fill_u32(uint32_t* __restrict__ p, uint64_t n, uint32_t value)
     p[i] = value;
 }
 
-template <int MODE, int S>
+// Launches a kernel on `s`, inside the table's persisting L2 window over the
+// free masks when it has one (a per-launch attribute: the stream is left as
+// it was).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_in_window(const Launch& L, void (*kern)(KArgs...), unsigned grid,
+                             unsigned block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  if (L.l2_bytes) {
+    at[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    at[0].val.accessPolicyWindow.base_ptr = L.l2_base;
+    at[0].val.accessPolicyWindow.num_bytes = L.l2_bytes;
+    at[0].val.accessPolicyWindow.hitRatio = L.l2_hit;
+    at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+template <int MODE, int S, bool DEFER = false>
 cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys,
                          const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
                          uint8_t* status, List ovf, const Launch& L, cudaStream_t s) {
@@ -2133,14 +2282,21 @@ cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys
   if (blocks == 0) blocks = 1;
   const OpPtrs a{ops, keys, vals, vals_out, found, status};
   const size_t smem = kStaged ? stage_smem(MODE, S) : 0;
-  k_ops<MODE, S><<<static_cast<unsigned>(blocks), kOpsThreads, smem, s>>>(v, a, n, ovf);
-  return cudaGetLastError();
+  if (MODE == kModeFind) {  // finds touch no free mask
+    k_ops<MODE, S, false><<<static_cast<unsigned>(blocks), kOpsThreads, smem, s>>>(v, a, n, ovf, 0);
+    return cudaGetLastError();
+  }
+  // mask prefetch when the batch could touch about one mask sector per 16
+  // buckets or more
+  const int pf = n * 16 >= v.nb ? 1 : 0;
+  return launch_in_window(L, k_ops<MODE, S, DEFER>, static_cast<unsigned>(blocks), kOpsThreads,
+                          smem, s, v, a, n, ovf, pf);
 }
 
 template <int S>
 cudaError_t launch_ops_s(int mode, const View& v, const uint8_t* ops, const uint32_t* keys,
                          const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
-                         uint8_t* status, List ovf, const Launch& L, cudaStream_t s) {
+                         uint8_t* status, List ovf, const Launch& L, cudaStream_t s, bool defer) {
   switch (mode) {
     case kModeFind:
       return launch_ops_t<kModeFind, S>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
@@ -2149,6 +2305,9 @@ cudaError_t launch_ops_s(int mode, const View& v, const uint8_t* ops, const uint
     case kModeErase:
       return launch_ops_t<kModeErase, S>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
     default:
+      if (defer)
+        return launch_ops_t<kModeMixed, S, true>(v, ops, keys, vals, n, vals_out, found, status, ovf,
+                                                 L, s);
       return launch_ops_t<kModeMixed, S>(v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
   }
 }
@@ -2174,10 +2333,10 @@ cudaError_t launch_fused(const View& v, const uint8_t* ops, const uint32_t* keys
 
 cudaError_t launch_ops(int mode, const View& v, const uint8_t* ops, const uint32_t* keys,
                        const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
-                       uint8_t* status, List ovf, const Launch& L, cudaStream_t s) {
+                       uint8_t* status, List ovf, const Launch& L, cudaStream_t s, bool defer) {
   if (v.S == 16)
-    return launch_ops_s<16>(mode, v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
-  return launch_ops_s<32>(mode, v, ops, keys, vals, n, vals_out, found, status, ovf, L, s);
+    return launch_ops_s<16>(mode, v, ops, keys, vals, n, vals_out, found, status, ovf, L, s, defer);
+  return launch_ops_s<32>(mode, v, ops, keys, vals, n, vals_out, found, status, ovf, L, s, defer);
 }
 
 cudaError_t launch_claim(const View& v, List in, uint64_t n, List out, uint8_t* status,
@@ -2188,21 +2347,24 @@ cudaError_t launch_claim(const View& v, List in, uint64_t n, List out, uint8_t* 
   const uint64_t cap = static_cast<uint64_t>(L.num_sms) * L.claim_blocks_per_sm;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
+  // prefetch the masks when the batch could read about one sector per 16
+  // buckets or more (a mixed batch of n ops holds at most n new keys)
+  const int pf = n * 16 >= v.nb ? 1 : 0;
   if (v.S == 16)
-    k_claim<16><<<static_cast<unsigned>(blocks), kClaimThreads, 0, s>>>(v, in, nchunks, out, status);
-  else
-    k_claim<32><<<static_cast<unsigned>(blocks), kClaimThreads, 0, s>>>(v, in, nchunks, out, status);
-  return cudaGetLastError();
+    return launch_in_window(L, k_claim<16>, static_cast<unsigned>(blocks), kClaimThreads, 0, s, v,
+                            in, nchunks, out, status, pf);
+  return launch_in_window(L, k_claim<32>, static_cast<unsigned>(blocks), kClaimThreads, 0, s, v, in,
+                          nchunks, out, status, pf);
 }
 
 cudaError_t launch_overflow(const View& v, List in, List pend, int resizable, uint8_t* status,
                             const Launch& L, cudaStream_t s) {
   const unsigned blocks = static_cast<unsigned>(L.num_sms * L.ovf_blocks_per_sm);
   if (v.S == 16)
-    k_overflow<16><<<blocks, kOvfThreads, 0, s>>>(v, in, pend, resizable, status);
-  else
-    k_overflow<32><<<blocks, kOvfThreads, 0, s>>>(v, in, pend, resizable, status);
-  return cudaGetLastError();
+    return launch_in_window(L, k_overflow<16>, blocks, kOvfThreads, 0, s, v, in, pend, resizable,
+                            status);
+  return launch_in_window(L, k_overflow<32>, blocks, kOvfThreads, 0, s, v, in, pend, resizable,
+                          status);
 }
 
 cudaError_t launch_maintenance(const View& v, cudaStream_t s) {
@@ -2314,27 +2476,30 @@ namespace {
 template <int S>
 cudaError_t occupancy_s(Launch* L) {
   int b = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeFind, S>,
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeFind, S, false>,
                                                                 kOpsThreads, 0);
   if (e != cudaSuccess) return e;
   L->ops_blocks_per_sm = b > 0 ? b : 1;
-  e = cudaFuncSetAttribute(k_ops<kModeFind, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_ops<kModeFind, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(stage_smem(kModeFind, S)));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ops<kModeInsert, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_ops<kModeInsert, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(stage_smem(kModeInsert, S)));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ops<kModeErase, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_ops<kModeErase, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(stage_smem(kModeErase, S)));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ops<kModeMixed, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_ops<kModeMixed, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(stage_smem(kModeMixed, S)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ops<kModeMixed, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(stage_smem(kModeMixed, S)));
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeInsert, S>, kOpsThreads,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeInsert, S, false>, kOpsThreads,
                                                     stage_smem(kModeInsert, S));
   if (e != cudaSuccess) return e;
   L->staged_blocks_per_sm = b > 0 ? b : 1;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeMixed, S>, kOpsThreads,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeMixed, S, false>, kOpsThreads,
                                                     stage_smem(kModeMixed, S));
   if (e != cudaSuccess) return e;
   L->staged1_blocks_per_sm = b > 0 ? b : 1;

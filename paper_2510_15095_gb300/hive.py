@@ -55,7 +55,8 @@ class Config(C.Structure):
                 ("shrink_num", C.c_uint32), ("shrink_den", C.c_uint32),
                 ("resizable", C.c_uint32), ("placement", C.c_uint32),
                 ("lock_spin_limit", C.c_uint32), ("blocks_per_sm", C.c_uint32),
-                ("map_on_demand", C.c_uint32)]
+                ("map_on_demand", C.c_uint32), ("l2_persist", C.c_uint32),
+                ("stage_wait_limit", C.c_uint32)]
 
 
 class Stats(C.Structure):
@@ -200,7 +201,7 @@ class HiveTable:
                  stash_permille: int = 10, grow=(9, 10), shrink=(2, 5),
                  placement: int = PLACE_BALANCED, lock_spin_limit: int | None = None,
                  blocks_per_sm: int = 0, bucket_slots: int = 32, map_on_demand: bool = False,
-                 stream=None):
+                 l2_persist: bool = False, stage_wait_limit: int = 0, stream=None):
         self._L = load_library()
         cfg = Config()
         self._L.hive_config_default(C.byref(cfg))
@@ -218,6 +219,8 @@ class HiveTable:
             cfg.lock_spin_limit = int(lock_spin_limit)
         cfg.blocks_per_sm = int(blocks_per_sm)
         cfg.map_on_demand = 1 if map_on_demand else 0
+        cfg.l2_persist = 1 if l2_persist else 0
+        cfg.stage_wait_limit = int(stage_wait_limit)
         self.config = cfg
         h = C.c_void_p()
         _raise(self._L, self._L.hive_create(C.byref(cfg), _stream_ptr(stream), C.byref(h)))
