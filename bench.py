@@ -40,7 +40,7 @@ SEED = 2
 L2_BYTES = 129 * 10**6  # GB300 L2
 # configurations the benchmark's tuner chooses among (fixed table, 95% load)
 BENCH_SPACE = {"bucket_slots": [16, 32], "placement": [0], "max_evictions": [16],
-               "blocks_per_sm": [4]}
+               "block_threads": [128, 256, 512], "l2_persist": [0, 1]}
 KERNEL_SRC = os.path.join(ROOT, "paper_2510_15095_gb300", "csrc", "hive_kernels.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 

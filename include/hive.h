@@ -115,6 +115,9 @@ typedef struct {
                                direct loads; 0 = 2^22 (default).  Only the
                                256-byte-bucket (S = 32) copies wait on an
                                mbarrier; a small value exercises the fallback */
+  uint32_t block_threads;   /* block shape of the bulk kernels: 128, 256 or 512
+                               threads (one op per lane); 0 = 256 (default; a
+                               tuning knob) */
 } hive_config;
 
 /* Per-table counters, accumulated since creation or the last hive_clear.

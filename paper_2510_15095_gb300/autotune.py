@@ -5,9 +5,12 @@ it times every candidate configuration on a synthetic workload of that class
 on the current GPU and caches the fastest in a JSON file.  The knobs:
 
 * bucket_slots S (Section III-B, 32 by default): 16, 32
-* max_evictions (cuckoo displacement bound, Section III-B): 4, 8, 16, 32
+* max_evictions (cuckoo displacement bound, Section III-B): 8, 16, 32
 * placement (two-choice policy): balanced, BitHash1-first (fixed tables)
-* blocks_per_sm (persistent grid of the bulk kernel): 3, 4
+* block_threads, the block shape of the bulk kernels: 128, 256, 512 threads
+  (one op per lane, so 4, 8 or 16 warps of 32 ops each)
+* l2_persist: the free masks in a persisting L2 window for the kernels that
+  claim slots, or not (fixed tables)
 * resize_batch K (bucket pairs per split/merge launch, Section IV-C), for
   resizable tables: 256, 1024, 4096, 8192
 
@@ -24,13 +27,13 @@ import time
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "hive_gb300", "autotune.json")
 
-FIXED_SPACE = {"bucket_slots": [16, 32], "max_evictions": [4, 8, 16, 32], "placement": [0, 1],
-               "blocks_per_sm": [3, 4]}
+FIXED_SPACE = {"bucket_slots": [16, 32], "max_evictions": [8, 16, 32], "placement": [0, 1],
+               "block_threads": [128, 256, 512], "l2_persist": [0, 1]}
 # Resizable tables keep the balanced placement: the BitHash1-first policy won
 # the tuner's short single-table runs but lost on the 1024-table leg (5.3
 # against 5.9 Gops/s batched).
 RESIZE_SPACE = {"bucket_slots": [16, 32], "resize_batch": [256, 1024, 4096, 8192], "max_evictions": [16],
-                "placement": [0]}
+                "placement": [0], "block_threads": [256]}
 LOAD_BANDS = (50, 80, 90, 95)
 
 

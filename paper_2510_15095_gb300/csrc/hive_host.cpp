@@ -481,10 +481,12 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
     return fail(HIVE_ERR_INVALID_ARG, "need 0 <= shrink < grow <= 1");
   if (cfg->stash_permille > 1000 || cfg->placement > HIVE_PLACE_FIRST || cfg->blocks_per_sm > 64 ||
       cfg->map_on_demand > 1 || cfg->l2_persist > 1 ||
+      (cfg->block_threads != 0 && cfg->block_threads != 128 && cfg->block_threads != 256 &&
+       cfg->block_threads != 512) ||
       cfg->resizable > 1)
     return fail(HIVE_ERR_INVALID_ARG,
-                "bad stash_permille, placement, resizable, blocks_per_sm, map_on_demand or "
-                "l2_persist");
+                "bad stash_permille, placement, resizable, blocks_per_sm, map_on_demand, "
+                "l2_persist or block_threads");
 
   hive_table* t = new (std::nothrow) hive_table();
   if (!t) return fail(HIVE_ERR_OOM, "host allocation failed");
@@ -513,6 +515,7 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
   t->stash_alloc = next_pow2(sc);
 
   cudaError_t e = cudaGetDevice(&t->device);
+  t->L.ops_threads = cfg->block_threads ? static_cast<int>(cfg->block_threads) : 256;
   if (e == cudaSuccess) e = query_occupancy(&t->L, static_cast<int>(S));
   if (e == cudaSuccess && cfg->blocks_per_sm) {
     const int cap = static_cast<int>(cfg->blocks_per_sm);

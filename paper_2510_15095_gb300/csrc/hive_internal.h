@@ -122,6 +122,7 @@ enum OpMode : int { kModeFind = 0, kModeInsert = 1, kModeErase = 2, kModeMixed =
 
 struct Launch {
   int num_sms;
+  int ops_threads;           // block shape of the bulk kernels: 128, 256 or 512 threads
   int ops_blocks_per_sm;     // bulk kernel, fragments loaded from global memory
   int staged_blocks_per_sm;  // bulk kernel, paired insert rounds staged in shared memory
   int staged1_blocks_per_sm; // bulk kernel, single-bucket rounds staged in shared memory

@@ -246,13 +246,20 @@ struct Geo {
 // the stage dead and redoes the round from global memory; before the warp
 // exits it waits up to kMbarSpinLimit tries for the copies still in flight.
 constexpr int kStageWords = 1024;
+// Staging words of a paired insert round: both buckets of kPairWords / (2 S)
+// ops per round (32 ops at S = 16 and 8 KB; fewer words split a chunk into
+// more rounds and leave more of the SM's on-chip memory to L1)
+#ifndef HIVE_PAIR_WORDS
+#define HIVE_PAIR_WORDS 1024
+#endif
+constexpr int kPairWords = HIVE_PAIR_WORDS;
 constexpr uint32_t kMbarSpinLimit = 1u << 22;
 
 // Staging words a warp of mode MODE needs: a paired insert round fills the
 // whole 8 KB; a single-bucket round holds 32 buckets (4 KB at S = 16), which
 // lets four 256-thread blocks share an SM.
 __host__ __device__ constexpr int stage_words(int mode, int S) {
-  return mode == kModeInsert ? kStageWords : 32 * S;
+  return mode == kModeInsert ? kPairWords : 32 * S;
 }
 // Shared-memory words per warp: its barrier, then its staging words.  (The
 // 64 KB of a paired round's block keeps three blocks within a 196 KB
@@ -262,11 +269,12 @@ __host__ __device__ constexpr int stage_words(int mode, int S) {
 __host__ __device__ constexpr int warp_smem_words(int mode, int S) {
   return 2 + stage_words(mode, S);
 }
-__host__ __device__ constexpr size_t stage_smem(int mode, int S) {
-  return static_cast<size_t>(kOpsThreads / 32) * 8u * warp_smem_words(mode, S);
+__host__ __device__ constexpr size_t stage_smem(int mode, int S, int threads = kOpsThreads) {
+  return static_cast<size_t>(threads / 32) * 8u * warp_smem_words(mode, S);
 }
 __host__ __device__ constexpr int staged_min_blocks(int mode, int S) {
-  return stage_words(mode, S) < kStageWords ? HIVE_STAGED_SMALL_MIN_BLOCKS : HIVE_STAGED_MIN_BLOCKS;
+  return (mode != kModeInsert && stage_words(mode, S) < kStageWords) ? HIVE_STAGED_SMALL_MIN_BLOCKS
+                                                                     : HIVE_STAGED_MIN_BLOCKS;
 }
 
 struct Stage {
@@ -316,14 +324,14 @@ __device__ __forceinline__ void stage_issue(const View& v, Stage& sg, unsigned n
     if ((need >> lane) & 1u)
       bulk_g2s(sg.buf + lane * S, v.buckets + static_cast<uint64_t>(x1) * S, kBucketBytes, sg.bar);
   } else {
-    constexpr int BO = kStageWords / (2 * S);
+    constexpr int BO = kPairWords / (2 * S);
 #pragma unroll
-    for (int k = 0; k < (2 * BO) / 32; ++k) {
+    for (int k = 0; k < (2 * BO + 31) / 32; ++k) {
       const int bi = lane + 32 * k;
-      const int op = o0 + (bi >> 1);
+      const int op = o0 + ((bi >> 1) & (BO - 1));
       const uint32_t y1 = __shfl_sync(kFull, x1, op & 31);
       const uint32_t y2 = __shfl_sync(kFull, x2, op & 31);
-      if ((need >> op) & 1u)
+      if (bi < 2 * BO && ((need >> op) & 1u))
         bulk_g2s(sg.buf + bi * S, v.buckets + static_cast<uint64_t>((bi & 1) ? y2 : y1) * S,
                  kBucketBytes, sg.bar);
     }
@@ -352,7 +360,7 @@ template <int S, bool PAIR>
 __device__ __forceinline__ void stage_issue_lsu(const View& v, Stage& sg, unsigned need, int o0,
                                                 uint32_t x1, uint32_t x2, int lane) {
   constexpr int L = Geo<S>::L, Q = Geo<S>::Q;  // lanes per bucket, buckets per instruction
-  constexpr int NB = PAIR ? 2 * (kStageWords / (2 * S)) : 32;  // buckets per round
+  constexpr int NB = PAIR ? 2 * (kPairWords / (2 * S)) : 32;  // buckets per round
   const int q = lane / L, ql = lane % L;
   __syncwarp();  // earlier reads of the buffer by any lane come first
 #pragma unroll 4
@@ -791,7 +799,7 @@ __device__ __forceinline__ void probe_pair_round(const View& v, unsigned need, u
                                                  int lane, bool& done, uint8_t& st, uint32_t& f1,
                                                  uint32_t& s1, uint32_t& f2, uint32_t& s2,
                                                  LaneCounters& cnt, Stage* sg) {
-  constexpr int BO = kStageWords / (2 * S);
+  constexpr int BO = kPairWords / (2 * S);
   constexpr unsigned BM = (BO >= 32) ? 0xFFFFFFFFu : ((1u << BO) - 1u);
   if (sg) {
     // free masks of both buckets, in flight beside the copies (unless the
@@ -1145,11 +1153,22 @@ __device__ __forceinline__ void run_chunk(const View& v, uint32_t stash_n, const
   }
 }
 
+// Resident blocks of THREADS threads per SM a bulk kernel is built for: the
+// warps per SM of the 256-thread shape (at least one block), which sets the
+// register budget of each shape.
+__host__ __device__ constexpr int ops_min_blocks(int mode, int S, int threads) {
+  return ((staged_mode(mode, S) ? staged_min_blocks(mode, S) : HIVE_OPS_MIN_BLOCKS) * kOpsThreads /
+              threads >
+          0)
+             ? (staged_mode(mode, S) ? staged_min_blocks(mode, S) : HIVE_OPS_MIN_BLOCKS) *
+                   kOpsThreads / threads
+             : 1;
+}
+
 // DEFER (mixed batches): the new keys are claimed by k_claim afterwards.
-template <int MODE, int S, bool DEFER>
-__global__ void __launch_bounds__(kOpsThreads, staged_mode(MODE, S)
-                                                   ? staged_min_blocks(MODE, S)
-                                                   : HIVE_OPS_MIN_BLOCKS)
+// THREADS: the block shape (128, 256 or 512 threads; a tuning knob).
+template <int MODE, int S, bool DEFER, int THREADS>
+__global__ void __launch_bounds__(THREADS, ops_min_blocks(MODE, S, THREADS))
     k_ops(View v, OpPtrs a, uint64_t n, List ovf, int prefetch_masks) {
   // claims and erases update free masks at random; a large batch first asks
   // L2 for the whole mask array in sequential pieces
@@ -2267,12 +2286,11 @@ cudaError_t launch_in_window(const Launch& L, void (*kern)(KArgs...), unsigned g
   return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
-template <int MODE, int S, bool DEFER = false>
-cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys,
-                         const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
-                         uint8_t* status, List ovf, const Launch& L, cudaStream_t s) {
+template <int MODE, int S, bool DEFER, int THREADS>
+cudaError_t launch_ops_tt(const View& v, const OpPtrs& a, uint64_t n, List ovf, const Launch& L,
+                          cudaStream_t s) {
   const uint64_t chunks = (n + 31) / 32;
-  const uint64_t warps_per_block = kOpsThreads / 32;
+  constexpr uint64_t warps_per_block = THREADS / 32;
   uint64_t blocks = (chunks + warps_per_block - 1) / warps_per_block;
   constexpr bool kStaged = staged_mode(MODE, S);
   const int per_sm = !kStaged ? L.ops_blocks_per_sm
@@ -2280,17 +2298,32 @@ cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys
   const uint64_t cap = static_cast<uint64_t>(L.num_sms) * per_sm;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
-  const OpPtrs a{ops, keys, vals, vals_out, found, status};
-  const size_t smem = kStaged ? stage_smem(MODE, S) : 0;
+  const size_t smem = kStaged ? stage_smem(MODE, S, THREADS) : 0;
   if (MODE == kModeFind) {  // finds touch no free mask
-    k_ops<MODE, S, false><<<static_cast<unsigned>(blocks), kOpsThreads, smem, s>>>(v, a, n, ovf, 0);
+    k_ops<MODE, S, false, THREADS><<<static_cast<unsigned>(blocks), THREADS, smem, s>>>(v, a, n,
+                                                                                        ovf, 0);
     return cudaGetLastError();
   }
   // mask prefetch when the batch could touch about one mask sector per 16
   // buckets or more
   const int pf = n * 16 >= v.nb ? 1 : 0;
-  return launch_in_window(L, k_ops<MODE, S, DEFER>, static_cast<unsigned>(blocks), kOpsThreads,
+  return launch_in_window(L, k_ops<MODE, S, DEFER, THREADS>, static_cast<unsigned>(blocks), THREADS,
                           smem, s, v, a, n, ovf, pf);
+}
+
+template <int MODE, int S, bool DEFER = false>
+cudaError_t launch_ops_t(const View& v, const uint8_t* ops, const uint32_t* keys,
+                         const uint32_t* vals, uint64_t n, uint32_t* vals_out, uint8_t* found,
+                         uint8_t* status, List ovf, const Launch& L, cudaStream_t s) {
+  const OpPtrs a{ops, keys, vals, vals_out, found, status};
+  switch (L.ops_threads) {
+    case 128:
+      return launch_ops_tt<MODE, S, DEFER, 128>(v, a, n, ovf, L, s);
+    case 512:
+      return launch_ops_tt<MODE, S, DEFER, 512>(v, a, n, ovf, L, s);
+    default:
+      return launch_ops_tt<MODE, S, DEFER, 256>(v, a, n, ovf, L, s);
+  }
 }
 
 template <int S>
@@ -2473,36 +2506,52 @@ cudaError_t launch_multi_gather(const MultiHdr* hdr, const View* views, const ui
 }
 
 namespace {
+// Shared-memory limits and resident blocks of the bulk kernels of one shape.
+template <int S, int T>
+cudaError_t occupancy_ops(Launch* L) {
+  int b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeFind, S, false, T>,
+                                                                T, 0);
+  if (e != cudaSuccess) return e;
+  L->ops_blocks_per_sm = b > 0 ? b : 1;
+  e = cudaFuncSetAttribute(k_ops<kModeFind, S, false, T>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(stage_smem(kModeFind, S, T)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ops<kModeInsert, S, false, T>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(stage_smem(kModeInsert, S, T)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ops<kModeErase, S, false, T>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(stage_smem(kModeErase, S, T)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ops<kModeMixed, S, false, T>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(stage_smem(kModeMixed, S, T)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ops<kModeMixed, S, true, T>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(stage_smem(kModeMixed, S, T)));
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeInsert, S, false, T>, T,
+                                                    stage_smem(kModeInsert, S, T));
+  if (e != cudaSuccess) return e;
+  L->staged_blocks_per_sm = b > 0 ? b : 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeMixed, S, false, T>, T,
+                                                    stage_smem(kModeMixed, S, T));
+  if (e != cudaSuccess) return e;
+  L->staged1_blocks_per_sm = b > 0 ? b : 1;
+  return cudaSuccess;
+}
+
 template <int S>
 cudaError_t occupancy_s(Launch* L) {
   int b = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeFind, S, false>,
-                                                                kOpsThreads, 0);
+  cudaError_t e = L->ops_threads == 128   ? occupancy_ops<S, 128>(L)
+                  : L->ops_threads == 512 ? occupancy_ops<S, 512>(L)
+                                          : occupancy_ops<S, 256>(L);
   if (e != cudaSuccess) return e;
-  L->ops_blocks_per_sm = b > 0 ? b : 1;
-  e = cudaFuncSetAttribute(k_ops<kModeFind, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(stage_smem(kModeFind, S)));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ops<kModeInsert, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(stage_smem(kModeInsert, S)));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ops<kModeErase, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(stage_smem(kModeErase, S)));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ops<kModeMixed, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(stage_smem(kModeMixed, S)));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ops<kModeMixed, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(stage_smem(kModeMixed, S)));
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeInsert, S, false>, kOpsThreads,
-                                                    stage_smem(kModeInsert, S));
-  if (e != cudaSuccess) return e;
-  L->staged_blocks_per_sm = b > 0 ? b : 1;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ops<kModeMixed, S, false>, kOpsThreads,
-                                                    stage_smem(kModeMixed, S));
-  if (e != cudaSuccess) return e;
-  L->staged1_blocks_per_sm = b > 0 ? b : 1;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused<S>, kOpsThreads, 0);
   if (e != cudaSuccess) return e;
   L->fused_blocks_per_sm = b > 0 ? b : 1;
@@ -2523,6 +2572,7 @@ cudaError_t occupancy_s(Launch* L) {
 }  // namespace
 
 cudaError_t query_occupancy(Launch* L, int S) {
+  if (L->ops_threads != 128 && L->ops_threads != 512) L->ops_threads = 256;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

@@ -56,7 +56,7 @@ class Config(C.Structure):
                 ("resizable", C.c_uint32), ("placement", C.c_uint32),
                 ("lock_spin_limit", C.c_uint32), ("blocks_per_sm", C.c_uint32),
                 ("map_on_demand", C.c_uint32), ("l2_persist", C.c_uint32),
-                ("stage_wait_limit", C.c_uint32)]
+                ("stage_wait_limit", C.c_uint32), ("block_threads", C.c_uint32)]
 
 
 class Stats(C.Structure):
@@ -201,7 +201,8 @@ class HiveTable:
                  stash_permille: int = 10, grow=(9, 10), shrink=(2, 5),
                  placement: int = PLACE_BALANCED, lock_spin_limit: int | None = None,
                  blocks_per_sm: int = 0, bucket_slots: int = 32, map_on_demand: bool = False,
-                 l2_persist: bool = False, stage_wait_limit: int = 0, stream=None):
+                 l2_persist: bool = False, stage_wait_limit: int = 0, block_threads: int = 0,
+                 stream=None):
         self._L = load_library()
         cfg = Config()
         self._L.hive_config_default(C.byref(cfg))
@@ -221,6 +222,7 @@ class HiveTable:
         cfg.map_on_demand = 1 if map_on_demand else 0
         cfg.l2_persist = 1 if l2_persist else 0
         cfg.stage_wait_limit = int(stage_wait_limit)
+        cfg.block_threads = int(block_threads)
         self.config = cfg
         h = C.c_void_p()
         _raise(self._L, self._L.hive_create(C.byref(cfg), _stream_ptr(stream), C.byref(h)))

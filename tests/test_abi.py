@@ -85,3 +85,20 @@ def test_host_validation_of_later_entry_points(lib):
     assert lib.hive32_insert(None, None, None, 3, None, None) == 1
     assert lib.hive32_find(None, None, 3, None, None, None) == 1
     assert lib.hive32_destroy(None) == 0
+
+
+def test_host_validation_of_tuning_fields(lib):
+    """The block shape and the L2-window flag are checked before any CUDA
+    call; their defaults are 0 (256 threads, no window)."""
+    from paper_2510_15095_gb300 import hive
+    cfg = hive.Config()
+    lib.hive_config_default(C.byref(cfg))
+    assert cfg.block_threads == 0 and cfg.l2_persist == 0 and cfg.stage_wait_limit == 0
+    h = C.c_void_p()
+    for field, bad in (("block_threads", 100), ("block_threads", 1024), ("block_threads", 64),
+                       ("l2_persist", 2)):
+        b = hive.Config()
+        lib.hive_config_default(C.byref(b))
+        setattr(b, field, bad)
+        assert lib.hive_create(C.byref(b), None, C.byref(h)) == 1, (field, bad)
+        assert b"block_threads" in lib.hive_last_error()

@@ -32,12 +32,15 @@ def test_tune_on_gpu(tmp_path):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     p = str(tmp_path / "tune.json")
-    space = {"max_evictions": [4, 16], "placement": [0, 1], "blocks_per_sm": [2, 4]}
+    # every block shape, the persisting L2 window on and off, and two bucket
+    # widths must give the same per-op results (tune() checks it)
+    space = {"max_evictions": [16], "placement": [0], "bucket_slots": [16, 32],
+             "block_threads": [128, 256, 512], "l2_persist": [0, 1]}
     cfg = A.tune(1 << 18, 95, (2, 1, 1), False, cache_path=p, space=space)
     assert set(cfg) == set(space)
     cache = A.load_cache(p)
     (entry,) = cache.values()
-    assert len(entry["candidates"]) == 8 and entry["gops"] > 0
+    assert len(entry["candidates"]) == 12 and entry["gops"] > 0
     # a second call is served from the cache
     assert A.tune(1 << 18, 95, (2, 1, 1), False, cache_path=p, space=space) == cfg
     rcfg = A.tune(1 << 18, 90, (4, 4, 2), True, cache_path=p,
