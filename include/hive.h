@@ -472,6 +472,30 @@ hive_status hive32_dump(hive32_table* t, hive32_image* img, void* stream);
 hive_status hive_check_batch(const uint8_t* h_ops, uint32_t op, const uint32_t* h_keys, uint64_t n,
                              uint32_t key_limit, uint64_t* first_bad);
 
+/* ---- Fault injection for tests (host side; the paper has none) ----
+ * The library's failure paths -- a bounded wait that gives up, a device
+ * allocation that fails -- are made to run by these two calls from the host.
+ * Neither makes the GPU fault or hang.
+ *
+ * hive_debug_fail_alloc: the n-th device allocation the library makes from
+ * now on (counted over every table of the process, n >= 1) fails as if the
+ * device were out of memory; n = 0 cancels a pending failure.  The call that
+ * made the allocation returns HIVE_ERR_OOM and leaves its table as it was
+ * (hive_create frees what it had allocated; an op call queues nothing and
+ * the table's data is untouched).  Always returns HIVE_OK.
+ *
+ * hive_debug_hold_lock: sets the bucket lock of `bucket` (Algorithm 3) to held
+ * (held != 0) or free (held == 0), stream-ordered on `stream`; bucket =
+ * UINT64_MAX sets every bucket in use.  An eviction round that needs a held
+ * lock gives up after lock_spin_limit tries: the chain puts the word it holds
+ * in the stash, the table's sticky error gets HIVE_ERR_TIMEOUT (hive_check)
+ * and hive_stats counts lock_timeouts.  Every result stays what the dictionary
+ * semantics give.  Free every held lock before the table is used without this
+ * hook again.  Returns INVALID_ARG for a bucket not in use, CUDA on a failed
+ * memset. */
+hive_status hive_debug_fail_alloc(uint32_t n);
+hive_status hive_debug_hold_lock(hive_table* t, uint64_t bucket, int held, void* stream);
+
 /* Text of the calling thread's last error (never NULL). */
 const char* hive_last_error(void);
 

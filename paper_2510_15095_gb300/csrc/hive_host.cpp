@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -146,11 +147,11 @@ hive_status ensure_lists(hive_table* t, uint64_t n, bool need_b = false) {
   const uint64_t cap = std::max<uint64_t>(next_pow2(std::max(n, t->list_cap)), 1u << 16);
   HIVE_CK(cudaDeviceSynchronize());
   free_lists(t);
-  cudaError_t e = cudaMalloc(&t->la_words, cap * sizeof(uint64_t));
-  if (e == cudaSuccess) e = cudaMalloc(&t->la_idx, cap * sizeof(uint32_t));
-  if (e == cudaSuccess && two) e = cudaMalloc(&t->lb_words, cap * sizeof(uint64_t));
-  if (e == cudaSuccess && two) e = cudaMalloc(&t->lb_idx, cap * sizeof(uint32_t));
-  if (e == cudaSuccess && two) e = cudaMalloc(&t->la_cnt, cap / 32);
+  cudaError_t e = dev_alloc(&t->la_words, cap * sizeof(uint64_t));
+  if (e == cudaSuccess) e = dev_alloc(&t->la_idx, cap * sizeof(uint32_t));
+  if (e == cudaSuccess && two) e = dev_alloc(&t->lb_words, cap * sizeof(uint64_t));
+  if (e == cudaSuccess && two) e = dev_alloc(&t->lb_idx, cap * sizeof(uint32_t));
+  if (e == cudaSuccess && two) e = dev_alloc(&t->la_cnt, cap / 32);
   if (e != cudaSuccess) {
     free_lists(t);
     return cuda_fail(e, "allocating op lists");
@@ -410,6 +411,20 @@ hive_status check_n(uint64_t n) {
 }  // namespace
 
 namespace hive {
+namespace {
+std::atomic<uint32_t> g_fail_alloc{0};  // 0: off; n: the n-th allocation from now fails
+}  // namespace
+cudaError_t dev_alloc_raw(void** p, size_t bytes) {
+  uint32_t c = g_fail_alloc.load();
+  while (c != 0 && !g_fail_alloc.compare_exchange_weak(c, c - 1)) {
+  }
+  if (c == 1) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+void set_fail_alloc(uint32_t n) { g_fail_alloc.store(n); }
 bool table_view(const hive_table* t, View* v, Launch* L, bool* resizable) {
   if (!t) return false;
   *v = make_view(t);
@@ -534,12 +549,12 @@ hive_status hive_create(const hive_config* cfg, void* stream, hive_table** out) 
     }
   }
   if (e == cudaSuccess && !t->vmm)
-    e = cudaMalloc(&t->buckets, t->nb_max * S * sizeof(uint64_t));
-  if (e == cudaSuccess) e = cudaMalloc(&t->masks, t->nb_max * sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&t->locks, 2 * t->nb_max * sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&t->stash_kv, t->stash_alloc * sizeof(uint64_t));
-  if (e == cudaSuccess) e = cudaMalloc(&t->stash_keys, t->stash_cap * sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&t->ctrl, sizeof(Ctrl));
+    e = dev_alloc(&t->buckets, t->nb_max * S * sizeof(uint64_t));
+  if (e == cudaSuccess) e = dev_alloc(&t->masks, t->nb_max * sizeof(uint32_t));
+  if (e == cudaSuccess) e = dev_alloc(&t->locks, 2 * t->nb_max * sizeof(uint32_t));
+  if (e == cudaSuccess) e = dev_alloc(&t->stash_kv, t->stash_alloc * sizeof(uint64_t));
+  if (e == cudaSuccess) e = dev_alloc(&t->stash_keys, t->stash_cap * sizeof(uint32_t));
+  if (e == cudaSuccess) e = dev_alloc(&t->ctrl, sizeof(Ctrl));
   if (e == cudaSuccess) e = cudaMallocHost(&t->host_ctrl, sizeof(Ctrl));
   if (e == cudaSuccess) {
     std::memset(t->host_ctrl, 0, sizeof(Ctrl));
@@ -818,8 +833,29 @@ hive_status hive_check(hive_table* t, void* stream) {
   HIVE_CK(cudaStreamSynchronize(s));
   if (err & kErrReserved) return fail(HIVE_ERR_RESERVED_KEY, "an op used a reserved key");
   if (err & kErrFull) return fail(HIVE_ERR_FULL, "an insert found no room (FULL)");
-  if (err & kErrTimeout) return fail(HIVE_ERR_TIMEOUT, "a bucket-lock wait gave up");
+  if (err & kErrTimeout)
+    return fail(HIVE_ERR_TIMEOUT, "a bounded wait gave up (bucket lock or staged copies)");
   if (err & kErrContract) return fail(HIVE_ERR_CONTRACT, "one key was updated twice in a call");
+  return HIVE_OK;
+}
+
+hive_status hive_debug_fail_alloc(uint32_t n) {
+  set_fail_alloc(n);
+  return HIVE_OK;
+}
+
+hive_status hive_debug_hold_lock(hive_table* t, uint64_t bucket, int held, void* stream) {
+  hive_status st = check_table(t);
+  if (st != HIVE_OK) return st;
+  if (bucket != UINT64_MAX && bucket >= t->nb)
+    return fail(HIVE_ERR_INVALID_ARG, "bucket is not in use");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // a held lock word is any non-zero value; bytes of 1 make 0x01010101
+  const int byte = held ? 1 : 0;
+  if (bucket == UINT64_MAX)
+    HIVE_CK(cudaMemsetAsync(t->locks, byte, t->nb * sizeof(uint32_t), s));
+  else
+    HIVE_CK(cudaMemsetAsync(t->locks + bucket, byte, sizeof(uint32_t), s));
   return HIVE_OK;
 }
 

@@ -43,11 +43,11 @@ hive_status ensure_staging(hive_table* t) {
   if (io.ready) return HIVE_OK;
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-    e = cudaMalloc(&io.ops[k], kChunkOps);
-    if (e == cudaSuccess) e = cudaMalloc(&io.keys[k], kChunkOps * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&io.vals[k], kChunkOps * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&io.out[k], kChunkOps * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&io.st[k], kChunkOps);
+    e = hive::dev_alloc(&io.ops[k], kChunkOps);
+    if (e == cudaSuccess) e = hive::dev_alloc(&io.keys[k], kChunkOps * 4);
+    if (e == cudaSuccess) e = hive::dev_alloc(&io.vals[k], kChunkOps * 4);
+    if (e == cudaSuccess) e = hive::dev_alloc(&io.out[k], kChunkOps * 4);
+    if (e == cudaSuccess) e = hive::dev_alloc(&io.st[k], kChunkOps);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io.in_ready[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io.done[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io.free[k], cudaEventDisableTiming);

@@ -298,6 +298,14 @@ void free_staging(hive_table* t);  // releases the host-buffer call staging
 // Resizable tables on virtual memory: back buckets [0, nb) with physical memory.
 hive_status ensure_committed(hive_table* t, cudaStream_t s);
 bool table_view(const hive_table* t, View* v, Launch* L, bool* resizable);
+// Every device allocation of the library goes through here, so that a test
+// can make one of them fail on the host (hive_debug_fail_alloc).
+cudaError_t dev_alloc_raw(void** p, size_t bytes);
+void set_fail_alloc(uint32_t n);  // hive_debug_fail_alloc
+template <class T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+  return dev_alloc_raw(reinterpret_cast<void**>(p), bytes);
+}
 void set_last_error(const std::string& msg);  // text returned by hive_last_error()
 // Batch-contract debugging (hive_contract.cpp): whether HIVE_DEBUG asks for
 // the check, and the check of a batch whose arrays the GPU addresses (copied

@@ -339,9 +339,15 @@ __device__ __forceinline__ void stage_issue(const View& v, Stage& sg, unsigned n
 }
 
 // Waits (bounded, warp-wide) for the copies of the round issued last.
+// A limit below 16 polls without suspending (mbarrier.test_wait), so that a
+// test can make the wait give up while the copies are certainly in flight.
 __device__ __forceinline__ bool stage_wait(const View& v, Stage& sg, int lane) {
   bool ok = false;
-  for (uint32_t it = 0; it < v.stage_spin_limit && !ok; ++it) ok = mbar_try_wait(sg.bar, sg.phase);
+  if (v.stage_spin_limit < 16) {
+    for (uint32_t it = 0; it < v.stage_spin_limit && !ok; ++it) ok = mbar_test_wait(sg.bar, sg.phase);
+  } else {
+    for (uint32_t it = 0; it < v.stage_spin_limit && !ok; ++it) ok = mbar_try_wait(sg.bar, sg.phase);
+  }
   sg.phase ^= 1u;
   if (__any_sync(kFull, !ok)) {  // never expected
     sg.dead = true;

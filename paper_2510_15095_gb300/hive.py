@@ -36,7 +36,7 @@ EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", 
            "hive32_config_default", "hive32_create", "hive32_destroy", "hive32_insert",
            "hive32_find", "hive32_erase", "hive32_execute", "hive32_size", "hive32_clear",
            "hive32_check",
-           "hive32_stats", "hive32_dump"]
+           "hive32_stats", "hive32_dump", "hive_debug_fail_alloc", "hive_debug_hold_lock"]
 KERNEL_KINDS = ["find", "insert", "erase", "mixed", "evict", "maint", "split", "merge", "count",
                 "fused", "claim"]
 
@@ -152,6 +152,8 @@ def load_library(path: str = LIB_PATH):
         L.hive32_stats.argtypes = [vp, C.POINTER(Stats), vp]
         L.hive32_dump.argtypes = [vp, C.POINTER(Image32), vp]
         L.hive_check_batch.argtypes = [vp, C.c_uint32, vp, u64, C.c_uint32, C.POINTER(u64)]
+        L.hive_debug_fail_alloc.argtypes = [C.c_uint32]
+        L.hive_debug_hold_lock.argtypes = [vp, u64, i32, vp]
         L.hive_last_error.argtypes = []
         L.hive_last_error.restype = C.c_char_p
         for name in EXPORTS:
@@ -394,6 +396,13 @@ class HiveTable:
         return {k: (float(p.ms[i]), int(p.launches[i])) for i, k in enumerate(KERNEL_KINDS)
                 if p.launches[i]}
 
+    def debug_hold_lock(self, bucket: int | None, held: bool, stream=None):
+        """hive_debug_hold_lock: hold or free one bucket lock (None: every
+        bucket in use), so that a test can make eviction waits give up."""
+        b = 0xFFFFFFFFFFFFFFFF if bucket is None else int(bucket)
+        _raise(self._L, self._L.hive_debug_hold_lock(self._h, b, 1 if held else 0,
+                                                     _stream_ptr(stream)))
+
     def dump(self, stream=None) -> dict:
         """Host image of the table (numpy arrays) for checks and checkpoints."""
         img = Image()
@@ -567,6 +576,13 @@ class HiveMulti:
             self.close()
         except Exception:
             pass
+
+
+def debug_fail_alloc(n: int):
+    """hive_debug_fail_alloc: the n-th device allocation of the library from
+    now on fails as out of memory (0 cancels)."""
+    L = load_library()
+    _raise(L, L.hive_debug_fail_alloc(int(n)))
 
 
 def check_batch(keys, ops=None, op: int = OP_INSERT, key_limit: int = 0xFFFFFFFE):
