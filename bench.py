@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -54,7 +55,7 @@ def parse_args():
     ap.add_argument("--slots", type=int, default=SLOTS)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=1 << 22,
+    ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE,
                     help="inserts (and as many finds) in the CPU oracle sample")
     ap.add_argument("--no-tables", action="store_true", help="skip the multi-table leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
@@ -214,6 +215,32 @@ def recorded_traffic(kernel: str):
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
 
+CPU_SAMPLE = 1 << 21  # inserts per oracle sample (and as many finds, a quarter as many mixed ops)
+
+
+def host_info() -> dict:
+    """The host the oracle runs on: logical CPUs and the CPU model."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.strip().lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"cpus": os.cpu_count(), "model": model or platform.machine()}
+
+
 def oracle_sample(w, n_sample: int):
     """Time the oracle on a prefix sample: n inserts, n finds, n/4 mixed ops."""
     import oracle
@@ -263,11 +290,11 @@ def run_reference(args, rank):
     if rank != 0:
         return
     w = make_workload(SEED, args.slots)
-    # bound the whole run: about 2^25 oracle ops over all steps
-    per_step = max(1 << 16, (1 << 25) // max(args.steps + args.warmup, 1) * 4 // 9)
-    n = min(args.cpu_sample, per_step, w["insert_keys"].size)
+    # each step times the same prefix sample as the own arm's cpu_baseline
+    # (about a second of single-threaded work per step)
+    n = min(args.cpu_sample, w["insert_keys"].size)
     for _ in range(args.warmup):
-        oracle_sample(w, n // 8)
+        oracle_sample(w, n)
     times, ops = [], 0
     for _ in range(args.steps):
         ops, dt = oracle_sample(w, n)
@@ -281,7 +308,7 @@ def run_reference(args, rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload_config(w, args.slots),
             "cpu_baseline": {"value": v, "unit": "Gops/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_info()},
             "e2e": {"value": v, "unit": "Gops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -677,26 +704,34 @@ def resize_leg(torch, H, dev, batches=32, n_batch=1 << 22, seed=60):
 # serving leg: continuous batching vs one launch per request
 # ---------------------------------------------------------------------------
 
-def serving_leg(torch, H, dev, n_tables=64, n_requests=3000, seed=50):
-    """64 resizable tables preloaded with 2^16 keys; requests of log-uniform
-    [1, 2^20] ops (insert:erase:find 40/20/40) on uniform random tables.
-    First both servers run closed-loop (every request available at once) to
-    find their saturation throughput; then Poisson arrivals at 70% of the
-    batched server's saturation request rate measure p50/p99 latency of both."""
+SERVING_RATES = (0.25, 0.5, 0.75, 0.9, 1.0, 1.2)  # x the batched server's saturation rate
+FIFO_RATES = (0.25, 0.5, 0.75, 0.9)               # x the FIFO reference's own saturation rate
+
+
+def serving_leg(torch, H, dev, n_tables=64, n_requests=3000, seed=50, preload_log2=22,
+                max_slots_log2=25):
+    """64 resizable tables preloaded with 2^preload_log2 keys each; requests of
+    log-uniform [1, 2^20] ops (insert:erase:find 40/20/40) on uniform random
+    tables.  Both servers first run closed-loop (every request available at
+    once) for their saturation throughput; then Poisson arrivals sweep the
+    batched server over SERVING_RATES x its saturation request rate, and the
+    FIFO reference over FIFO_RATES x its own (above its saturation its queue
+    only grows).  Every run must give every request the same results."""
     from paper_2510_15095_gb300 import serving as SV
     from paper_2510_15095_gb300 import workload as W
-    pre = 1 << 16
+    pre = 1 << preload_log2
 
     from paper_2510_15095_gb300 import autotune as AT
     tuned = AT.tune(1 << 20, 90, (2, 1, 1), True)  # the multi-table leg's class
     knobs = {"bucket_slots": int(tuned.get("bucket_slots", 32)),
              "max_evictions": int(tuned.get("max_evictions", 16)),
              "placement": int(tuned.get("placement", 0))}
+    init_slots = 1 << (preload_log2 + 1)
 
     def fresh():
         tabs = []
         for t in range(n_tables):
-            tb = H.HiveTable(1 << 17, max_slots=1 << 23, resizable=True,
+            tb = H.HiveTable(init_slots, max_slots=1 << max_slots_log2, resizable=True,
                              resize_batch=int(tuned.get("resize_batch", 1024)), **knobs)
             k, v = W.preload_t(torch, 1000 + t, pre, dev)
             tb.insert(k, v, status=False)
@@ -711,6 +746,8 @@ def serving_leg(torch, H, dev, n_tables=64, n_requests=3000, seed=50):
         return [SV.Request(r.rid, r.table, float(a), r.ops, r.keys, r.vals, r.n_insert)
                 for r, a in zip(base, arr)]
 
+    sizes = {}
+
     def serve(reqs, fifo):
         tabs = fresh()
         torch.cuda.synchronize(dev)
@@ -721,32 +758,64 @@ def serving_leg(torch, H, dev, n_tables=64, n_requests=3000, seed=50):
                                 max_batch_reqs=256, depth=2)
             out = srv.run(reqs)
             srv.close()
+        sizes["live"] = [tb.size() for tb in tabs]
+        sizes["slots"] = [tb.capacity() for tb in tabs]
         for tb in tabs:
             tb.close()
         return out
 
+    ref, same = [], [True]
+
+    def check(reqs):
+        if not ref:
+            ref.extend((r.status.clone(), r.vals_out.clone()) for r in reqs)
+        else:
+            same[0] = same[0] and all(torch.equal(a, r.status) and torch.equal(b, r.vals_out)
+                                      for (a, b), r in zip(ref, reqs))
+        for r in reqs:
+            r.status = r.vals_out = None
+
+    def poisson(rate, salt):
+        gaps = np.random.default_rng(seed + salt).exponential(1.0 / rate, n_requests)
+        return np.cumsum(gaps) - gaps[0]
+
     zeros = np.zeros(n_requests)
-    sat_b_reqs = with_arrivals(zeros)
-    sat_b = serve(sat_b_reqs, False)
-    sat_f_reqs = with_arrivals(zeros)
-    sat_f = serve(sat_f_reqs, True)
-    same = all(torch.equal(a.status, b.status) and torch.equal(a.vals_out, b.vals_out)
-               for a, b in zip(sat_b_reqs, sat_f_reqs))
-    rate = 0.7 * n_requests / sat_b["makespan_s"]
-    gaps = np.random.default_rng(seed + 1).exponential(1.0 / rate, n_requests)
-    arr = np.cumsum(gaps) - gaps[0]
-    lat_b = serve(with_arrivals(arr), False)
-    lat_f = serve(with_arrivals(arr), True)
+    reqs = with_arrivals(zeros)
+    sat_b = serve(reqs, False)
+    check(reqs)
+    end_live, end_slots = sizes["live"], sizes["slots"]
+    reqs = with_arrivals(zeros)
+    sat_f = serve(reqs, True)
+    check(reqs)
     keep = ("p50_ms", "p99_ms", "mean_ms", "gops", "batches", "mean_batch_requests", "rejected")
-    return {"workload": (f"{n_tables} resizable tables preloaded with 2^16 keys, {n_requests} "
-                         "requests of log-uniform 1-2^20 ops (insert:erase:find 40/20/40), HBM "
-                         "budget 64 GB"),
+    sat_rate_b = n_requests / sat_b["makespan_s"]
+    sat_rate_f = n_requests / sat_f["makespan_s"]
+    rates = []
+    for i, f in enumerate(SERVING_RATES):
+        reqs = with_arrivals(poisson(f * sat_rate_b, 1 + i))
+        out = serve(reqs, False)
+        check(reqs)
+        rates.append({"server": "batched", "rate_x_saturation": f, "req_per_s": f * sat_rate_b,
+                      **{k: out[k] for k in keep}})
+    for i, f in enumerate(FIFO_RATES):
+        reqs = with_arrivals(poisson(f * sat_rate_f, 11 + i))
+        out = serve(reqs, True)
+        check(reqs)
+        rates.append({"server": "fifo", "rate_x_saturation": f, "req_per_s": f * sat_rate_f,
+                      **{k: out[k] for k in keep}})
+    return {"workload": (f"{n_tables} resizable tables preloaded with 2^{preload_log2} keys "
+                         f"(growth limit 2^{max_slots_log2} slots each), {n_requests} requests of "
+                         "log-uniform 1-2^20 ops (insert:erase:find 40/20/40), HBM budget 64 GB"),
             "ops": int(sat_b["ops"]),
             "saturation": {"batched_gops": sat_b["gops"], "fifo_gops": sat_f["gops"],
-                           "speedup": sat_b["gops"] / sat_f["gops"]},
-            "poisson_rate_req_per_s": rate,
-            "batched": {k: lat_b[k] for k in keep}, "fifo": {k: lat_f[k] for k in keep},
-            "identical_results": bool(same), "tuned": tuned}
+                           "speedup": sat_b["gops"] / sat_f["gops"],
+                           "batched_req_per_s": sat_rate_b, "fifo_req_per_s": sat_rate_f},
+            "rates": rates,
+            "tables_at_end": {"live_keys_min": int(min(end_live)),
+                              "live_keys_max": int(max(end_live)),
+                              "slots_max": int(max(end_slots)),
+                              "committed_gb": float(sum(end_slots) * SV.SLOT_BYTES / 1e9)},
+            "identical_results": bool(same[0]), "tuned": tuned}
 
 
 # ---------------------------------------------------------------------------
@@ -995,7 +1064,8 @@ def main():
         ops, dt = oracle_sample(w, n)
         cpu = {"value": ops / dt / 1e9, "unit": "Gops/s", "cores": 1, "kind": "oracle",
                "sample": f"{n} inserts + {n} finds + {n // 4} mixed ops (prefix of the workload), "
-                         f"{dt:.1f} s single-threaded std::unordered_map"}
+                         f"{dt:.1f} s single-threaded std::unordered_map",
+               "host": host_info()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gops/s", "n_gpus": world,

@@ -357,6 +357,16 @@ hive_status hive_multi_execute(hive_multi* m, const hive_segment* segs, uint32_t
 /* Frees the group (not its tables).  Synchronises the device first. */
 hive_status hive_multi_destroy(hive_multi* m);
 
+/* Upper bounds of the live sizes of the group's first n_tables tables, into
+ * out[n_tables]: the size gathered after the newest completed batch of each
+ * table plus the inserts of its batches queued since (HIVE_MULTI_ASYNC), or
+ * the exact sizes (synchronous groups).  A scheduler that admits work by
+ * memory uses these, and hive_capacity() of each table, instead of counting
+ * inserts itself: erases make the bounds fall again.  Host-side; it queries
+ * the batches' events and never waits.  INVALID_ARG for NULL pointers or
+ * n_tables above the group's. */
+hive_status hive_multi_bounds(hive_multi* m, uint64_t* out, uint32_t n_tables);
+
 /* Insert into a FIXED-capacity table without allocating anything.  The paper
  * has no counterpart; this is a library convenience.  Same inputs, outputs and
  * results as hive_insert, for callers that must not call cudaMalloc: a process

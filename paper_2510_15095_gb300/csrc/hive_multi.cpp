@@ -267,6 +267,14 @@ hive_status hive_multi_destroy(hive_multi* m) {
   return HIVE_OK;
 }
 
+hive_status hive_multi_bounds(hive_multi* m, uint64_t* out, uint32_t n_tables) {
+  if (!m || !out) return mfail(HIVE_ERR_INVALID_ARG, "group and out must not be NULL");
+  if (n_tables > m->tables.size()) return mfail(HIVE_ERR_INVALID_ARG, "n_tables above the group's");
+  if (m->async) refresh_bounds(m);
+  for (uint32_t t = 0; t < n_tables; ++t) out[t] = m->async ? m->ub[t] : m->tables[t]->size_host;
+  return HIVE_OK;
+}
+
 hive_status hive_multi_execute(hive_multi* m, const hive_segment* segs, uint32_t n_segs,
                                void* stream) {
   if (!m) return mfail(HIVE_ERR_INVALID_ARG, "multi is NULL");

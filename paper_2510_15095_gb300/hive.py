@@ -31,7 +31,7 @@ EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", 
            "hive_erase", "hive_execute", "hive_execute_fused", "hive_size", "hive_capacity", "hive_clear", "hive_check",
            "hive_stats", "hive_dump", "hive_profile_enable", "hive_profile_read",
            "hive_insert_noalloc", "hive_multi_create", "hive_multi_execute",
-           "hive_multi_destroy", "hive_insert_host", "hive_find_host", "hive_execute_host",
+           "hive_multi_destroy", "hive_multi_bounds", "hive_insert_host", "hive_find_host", "hive_execute_host",
            "hive_reserve", "hive_memory", "hive_check_batch", "hive_last_error",
            "hive32_config_default", "hive32_create", "hive32_destroy", "hive32_insert",
            "hive32_find", "hive32_erase", "hive32_execute", "hive32_size", "hive32_clear",
@@ -136,6 +136,7 @@ def load_library(path: str = LIB_PATH):
                                         C.POINTER(vp)]
         L.hive_multi_execute.argtypes = [vp, C.POINTER(Segment), C.c_uint32, vp]
         L.hive_multi_destroy.argtypes = [vp]
+        L.hive_multi_bounds.argtypes = [vp, C.POINTER(u64), C.c_uint32]
         L.hive_profile_enable.argtypes = [vp, i32]
         L.hive_profile_read.argtypes = [vp, C.POINTER(Profile)]
         L.hive32_config_default.argtypes = [C.POINTER(Config32)]
@@ -565,6 +566,14 @@ class HiveMulti:
             arr[i].vals_out = _dptr(g.get("vals_out"), 4, n, "vals_out")
             arr[i].status = _dptr(g.get("status"), 1, n, "status")
         _raise(self._L, self._L.hive_multi_execute(self._h, arr, len(segs), _stream_ptr(stream)))
+
+    def bounds(self) -> list:
+        """hive_multi_bounds: upper bounds of the tables' live sizes (host
+        side; never waits)."""
+        n = len(self.tables)
+        out = (C.c_uint64 * max(n, 1))()
+        _raise(self._L, self._L.hive_multi_bounds(self._h, out, n))
+        return [int(out[i]) for i in range(n)]
 
     def close(self):
         if getattr(self, "_h", None):

@@ -70,8 +70,10 @@ class HiveServer:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.multi = H.HiveMulti(self.tables, max_segments=self.max_reqs, max_ops=self.max_ops,
                                  use_graph=use_graph, asynchronous=True, stream=self.stream)
-        # upper bounds of sizes and capacities, kept on the host; a table grows
-        # in steps of K bucket pairs, so a growth may overshoot by K buckets
+        # upper bounds of sizes and capacities, kept on the host between
+        # batches and refreshed from the library before each batch is formed;
+        # a table grows in steps of K bucket pairs, so a growth may overshoot
+        # by K buckets
         self.size_ub = [t.size() for t in self.tables]
         self.cap_slots = [t.capacity() for t in self.tables]
         self.slack = [32 * int(t.config.resize_batch) for t in self.tables]
@@ -89,6 +91,14 @@ class HiveServer:
 
     def _committed_bytes(self) -> float:
         return sum(self.cap_slots) * SLOT_BYTES
+
+    def _sync_bounds(self):
+        """Take the size bounds the library keeps (the size gathered after each
+        table's newest completed batch plus the inserts queued since, so erases
+        lower them again) and the tables' capacities (which include the growth
+        planned for batches in flight)."""
+        self.size_ub = self.multi.bounds()
+        self.cap_slots = [t.capacity() for t in self.tables]
 
     def _form_batch(self, pending: deque, reqs):
         chosen, tables_in, blocked = [], set(), set()
@@ -122,14 +132,22 @@ class HiveServer:
             pending.extend(tmp)
         return chosen
 
+    def _note_launch(self, chosen, reqs):
+        """Host bookkeeping of a batch about to be queued: its tables' bounds
+        rise by the batch's inserts and their capacities by the growth it may
+        need, until the next _sync_bounds()."""
+        for rid in chosen:
+            r = reqs[rid]
+            self.cap_slots[r.table] = self._needed_slots(r.table, r.n_insert)
+            self.size_ub[r.table] += r.n_insert
+
     def _launch(self, chosen, reqs):
         segs = []
         for rid in chosen:
             r = reqs[rid]
             segs.append({"table": r.table, "ops": r.ops, "keys": r.keys, "vals": r.vals,
                          "vals_out": r.vals_out, "status": r.status, "n_insert": r.n_insert})
-            self.cap_slots[r.table] = self._needed_slots(r.table, r.n_insert)
-            self.size_ub[r.table] += r.n_insert
+        self._note_launch(chosen, reqs)
         self.multi.execute(segs, stream=self.stream)
         ev = self.torch.cuda.Event(enable_timing=True)
         ev.record(self.stream)
@@ -164,6 +182,7 @@ class HiveServer:
                     reqs[rid].done_at = done_at
                 n_done += len(ids)
             if pending and len(inflight) < self.depth:
+                self._sync_bounds()
                 chosen = self._form_batch(pending, reqs)
                 if chosen:
                     inflight.append((self._launch(chosen, reqs), chosen))

@@ -32,6 +32,7 @@ def test_reference_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert cb["unit"] == "Gops/s" and cb["sample"]
+    assert cb["host"]["cpus"] == os.cpu_count() and cb["host"]["model"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

@@ -69,3 +69,54 @@ def test_hbm_budget_blocks_a_growing_table_and_its_later_requests():
     pending = deque(range(3))
     assert s._form_batch(pending, reqs) == [1]
     assert list(pending) == [0, 2]  # table 0 keeps its FIFO order behind the blocked request
+
+
+class _FlatGroup:
+    """Stands in for the library's multi-table group: erases balance the
+    inserts, so every table's live size stays where it started."""
+
+    def __init__(self, sizes):
+        self.sizes = list(sizes)
+
+    def bounds(self):
+        return list(self.sizes)
+
+
+class _Table:
+    def __init__(self, slots):
+        self.slots = slots
+
+    def capacity(self):
+        return self.slots
+
+
+def test_flat_live_size_is_never_rejected():
+    """40/20/40-style traffic whose erases keep the live size flat: the
+    admission bound is refreshed from the library before each batch, so a
+    long run of inserting requests never outgrows a budget that the live size
+    fits in (counting inserts alone would pass it after a few batches)."""
+    slot = SV.SLOT_BYTES
+    s = server(1, [1024], [880], budget=1200 * slot, slack=64)
+    s.multi = _FlatGroup([880])
+    s.tables = [_Table(1024)]
+    reqs = [req(i, 0, 40, 40) for i in range(50)]
+    pending = deque(range(50))
+    launched = []
+    while pending:
+        s._sync_bounds()
+        chosen = s._form_batch(pending, reqs)
+        assert chosen, f"request {pending[0]} would be rejected"
+        s._note_launch(chosen, reqs)
+        launched += chosen
+    assert launched == list(range(50))
+    # without the refresh the insert count alone exhausts the budget
+    s = server(1, [1024], [880], budget=1200 * slot, slack=64)
+    pending = deque(range(50))
+    blocked = False
+    while pending:
+        chosen = s._form_batch(pending, reqs)
+        if not chosen:
+            blocked = True
+            break
+        s._note_launch(chosen, reqs)
+    assert blocked
