@@ -257,6 +257,16 @@ hive_status hive_reserve(hive_table* t, uint64_t slots, void* stream);
  * other arrays are allocated at their maximum).  Host-side, no sync. */
 hive_status hive_memory(hive_table* t, uint64_t* committed, uint64_t* reserved);
 
+/* The two hash mixes of Section III-C on the device: h1_out[i] = BitHash1(keys[i])
+ * and h2_out[i] = BitHash2(keys[i]), the full 32-bit mixes before any bucket
+ * reduction (the tables address buckets with the linear-hashing rule of
+ * Section IV-C on these values).  Device arrays of n entries owned by the
+ * caller; either output may be NULL.  Stream-ordered, no synchronisation.
+ * For callers that place or shard keys the way the tables do, and for tests
+ * of the mixes.  INVALID_ARG for NULL keys or two NULL outputs with n > 0. */
+hive_status hive_hash(const uint32_t* keys, uint64_t n, uint32_t* h1_out, uint32_t* h2_out,
+                      void* stream);
+
 /* Current slot capacity S * nBuckets (host-side state, no synchronisation). */
 hive_status hive_capacity(hive_table* t, uint64_t* slots_out);
 
@@ -379,7 +389,10 @@ hive_status hive_multi_bounds(hive_multi* m, uint64_t* out, uint32_t n_tables);
  *    is queued; a resizable table also gives HIVE_ERR_INVALID_ARG.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept with the id of the CUDA
+ *    context it belongs to and looked up again when the current context
+ *    differs (after cudaDeviceReset the array may move); where the driver
+ *    gives no context ids, every call looks it up.
  *  - All calls share the array: calls whose work overlaps on the GPU (e.g. on
  *    two streams at once) race and must not be issued. */
 hive_status hive_insert_noalloc(hive_table* t, const uint32_t* keys, const uint32_t* vals,

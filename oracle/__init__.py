@@ -71,6 +71,8 @@ def lib():
             L.orc_lh_address.argtypes = [u32, u32, u32]
             L.orc_lh_address.restype = u32
             L.orc_bithash_many.argtypes = [C.c_int, vp, vp, u64]
+            L.orc_bithash_checksum.argtypes = [u64, u64]
+            L.orc_bithash_checksum.restype = u64
             L.orc_lh_address_many.argtypes = [vp, vp, u64, u32, u32]
             P = C.POINTER(LHState)
             L.orc_lh_init.argtypes = [P, u64, u64, u32, u32, u32, u32, u32, u32]
@@ -178,6 +180,12 @@ def bithash_many(which: int, keys) -> np.ndarray:
     out = np.empty(k.size, np.uint32)
     lib().orc_bithash_many(which, _ptr(k), _ptr(out), k.size)
     return out
+
+
+def bithash_checksum(lo: int, hi: int) -> int:
+    """Sum over keys lo..hi-1 of (BitHash1(k) + 2^32 BitHash2(k)) * (2k + 1)
+    modulo 2^64 (see orc_bithash_checksum)."""
+    return int(lib().orc_bithash_checksum(int(lo), int(hi)))
 
 
 def lh_address_many(h, M: int, p: int) -> np.ndarray:

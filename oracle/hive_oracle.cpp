@@ -193,6 +193,23 @@ void orc_bithash_many(int which, const uint32_t* in, uint32_t* out, uint64_t n) 
   for (uint64_t i = 0; i < n; ++i) out[i] = which == 1 ? orc_bithash1(in[i]) : orc_bithash2(in[i]);
 }
 
+// A position-weighted sum of both mixes over every key of [lo, hi) (keys are
+// the 32-bit values lo..hi-1, hi <= 2^32), modulo 2^64:
+//   sum_k (BitHash1(k) + 2^32 BitHash2(k)) * (2k + 1).
+// Every weight is odd, so one wrong output anywhere changes the sum; a test
+// compares it with the same sum over the GPU's outputs to check both mixes on
+// all 2^32 keys without moving the outputs to the host.
+uint64_t orc_bithash_checksum(uint64_t lo, uint64_t hi) {
+  uint64_t acc = 0;
+  for (uint64_t k = lo; k < hi; ++k) {
+    const uint32_t x = static_cast<uint32_t>(k);
+    const uint64_t w = static_cast<uint64_t>(orc_bithash1(x)) |
+                       (static_cast<uint64_t>(orc_bithash2(x)) << 32);
+    acc += w * (2 * k + 1);
+  }
+  return acc;
+}
+
 // ---------------------------------------------------------------------------
 // 3. Linear hashing (Section IV-C).  Buckets below the split pointer p have
 //    already been split in this round and are addressed with one more hash bit.

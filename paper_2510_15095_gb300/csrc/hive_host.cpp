@@ -839,6 +839,15 @@ hive_status hive_check(hive_table* t, void* stream) {
   return HIVE_OK;
 }
 
+hive_status hive_hash(const uint32_t* keys, uint64_t n, uint32_t* h1_out, uint32_t* h2_out,
+                      void* stream) {
+  if (n == 0) return HIVE_OK;
+  if (!keys || (!h1_out && !h2_out))
+    return fail(HIVE_ERR_INVALID_ARG, "keys and at least one output must not be NULL");
+  HIVE_CK(launch_hash(keys, n, h1_out, h2_out, static_cast<cudaStream_t>(stream)));
+  return HIVE_OK;
+}
+
 hive_status hive_debug_fail_alloc(uint32_t n) {
   set_fail_alloc(n);
   return HIVE_OK;

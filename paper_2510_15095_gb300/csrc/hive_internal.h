@@ -169,6 +169,8 @@ cudaError_t launch_multi_maint(int S, const MultiHdr* hdr, const View* views,
 cudaError_t launch_multi_split(int S, const MultiJob* jobs, uint32_t n_jobs, uint32_t total_pairs,
                                const View* views, cudaStream_t s);
 cudaError_t launch_fill_u32(uint32_t* p, uint64_t n, uint32_t value, cudaStream_t s);
+cudaError_t launch_hash(const uint32_t* keys, uint64_t n, uint32_t* h1, uint32_t* h2,
+                        cudaStream_t s);
 cudaError_t launch_multi_gather(const MultiHdr* hdr, const View* views, const uint32_t* touched,
                                 uint32_t max_tables, unsigned long long* out, cudaStream_t s);
 cudaError_t query_occupancy(Launch* L, int S);

@@ -2261,6 +2261,17 @@ __global__ void k_multi_gather(const MultiHdr* __restrict__ hdr, const View* __r
   out[2 * t + 1] = (static_cast<unsigned long long>(c->err) << 32) | c->stash_claims;
 }
 
+// BitHash1 and BitHash2 of n keys (hive_hash).
+__global__ void k_hash(const uint32_t* __restrict__ keys, uint64_t n, uint32_t* __restrict__ h1,
+                       uint32_t* __restrict__ h2) {
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const uint32_t k = __ldcs(keys + i);
+    if (h1) __stcs(h1 + i, bithash1(k));
+    if (h2) __stcs(h2 + i, bithash2(k));
+  }
+}
+
 __global__ void k_fill_u32(uint32_t* __restrict__ p, uint64_t n, uint32_t value) {
   for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
@@ -2451,6 +2462,15 @@ cudaError_t launch_count_inserts(const uint8_t* ops, uint64_t n, unsigned* out, 
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   k_count_inserts<<<static_cast<unsigned>(blocks), 256, 0, s>>>(ops, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hash(const uint32_t* keys, uint64_t n, uint32_t* h1, uint32_t* h2,
+                        cudaStream_t s) {
+  if (!n) return cudaSuccess;
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_hash<<<static_cast<unsigned>(blocks), 256, 0, s>>>(keys, n, h1, h2);
   return cudaGetLastError();
 }
 

@@ -16,6 +16,7 @@
 // exits.  All calls share it and it keeps the last call's contents, so each
 // call clears the list counter first, and calls whose work overlaps on the
 // GPU (for example on two streams) race on it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -37,23 +38,71 @@ struct NoAllocScratch {
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 // Device address of g_noalloc_scratch per device.  In host code the symbol is
-// only a host-side stand-in, so its address is asked of the runtime once per
-// device, with that device current, on the first call there.
+// only a host-side stand-in, so its address is asked of the runtime, with the
+// device current, on the first call there.  The answer belongs to the CUDA
+// context that loaded the module: after cudaDeviceReset the next call runs in
+// a new context, where the array may sit elsewhere.  So the cached address is
+// kept with the id of the context it came from (cuCtxGetId) and asked again
+// when the current context's id differs; where the driver offers no context
+// ids, the address is asked on every call.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 NoAllocScratch* g_addr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};
+
+struct CtxIds {
+  bool ok = false;
+  CUresult (*current)(CUcontext*) = nullptr;
+  CUresult (*id)(CUcontext, unsigned long long*) = nullptr;
+};
+
+template <class F>
+bool fetch_entry(const char* name, F* out) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q{};
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !p) {
+    cudaGetLastError();
+    return false;
+  }
+  *out = reinterpret_cast<F>(p);
+  return true;
+}
+
+const CtxIds& ctx_ids() {
+  static CtxIds c = [] {
+    CtxIds r;
+    r.ok = fetch_entry("cuCtxGetCurrent", &r.current) && fetch_entry("cuCtxGetId", &r.id);
+    return r;
+  }();
+  return c;
+}
+
+// Id of the calling thread's current context (0: unknown).
+unsigned long long current_ctx_id() {
+  const CtxIds& c = ctx_ids();
+  if (!c.ok) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (c.current(&ctx) != CUDA_SUCCESS || !ctx || c.id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 cudaError_t scratch_address(NoAllocScratch** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  // cudaGetDevice leaves the device's primary context current for the
+  // runtime, so the id read next is the one kernels of this call run in
+  const unsigned long long ctx = current_ctx_id();
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  if (!g_addr[dev] || ctx == 0 || ctx != g_ctx_id[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_addr[dev] = static_cast<NoAllocScratch*>(p);
+    g_ctx_id[dev] = ctx;
   }
   *out = g_addr[dev];
   return cudaSuccess;

@@ -36,7 +36,7 @@ EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", 
            "hive32_config_default", "hive32_create", "hive32_destroy", "hive32_insert",
            "hive32_find", "hive32_erase", "hive32_execute", "hive32_size", "hive32_clear",
            "hive32_check",
-           "hive32_stats", "hive32_dump", "hive_debug_fail_alloc", "hive_debug_hold_lock"]
+           "hive32_stats", "hive32_dump", "hive_debug_fail_alloc", "hive_debug_hold_lock", "hive_hash"]
 KERNEL_KINDS = ["find", "insert", "erase", "mixed", "evict", "maint", "split", "merge", "count",
                 "fused", "claim"]
 
@@ -154,6 +154,7 @@ def load_library(path: str = LIB_PATH):
         L.hive32_dump.argtypes = [vp, C.POINTER(Image32), vp]
         L.hive_check_batch.argtypes = [vp, C.c_uint32, vp, u64, C.c_uint32, C.POINTER(u64)]
         L.hive_debug_fail_alloc.argtypes = [C.c_uint32]
+        L.hive_hash.argtypes = [vp, u64, vp, vp, vp]
         L.hive_debug_hold_lock.argtypes = [vp, u64, i32, vp]
         L.hive_last_error.argtypes = []
         L.hive_last_error.restype = C.c_char_p
@@ -585,6 +586,19 @@ class HiveMulti:
             self.close()
         except Exception:
             pass
+
+
+def hash_keys(keys, stream=None):
+    """hive_hash: (BitHash1, BitHash2) of every key of a CUDA tensor with
+    32-bit elements, as int32 tensors holding the unsigned mixes."""
+    torch = _torch()
+    L = load_library()
+    n = keys.numel()
+    h1 = torch.empty(n, dtype=torch.int32, device=keys.device)
+    h2 = torch.empty(n, dtype=torch.int32, device=keys.device)
+    _raise(L, L.hive_hash(_dptr(keys, 4, n, "keys"), n, _dptr(h1, 4, n, "h1"),
+                          _dptr(h2, 4, n, "h2"), _stream_ptr(stream)))
+    return h1, h2
 
 
 def debug_fail_alloc(n: int):

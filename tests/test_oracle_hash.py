@@ -115,3 +115,17 @@ def test_csr_near_one_at_unit_load(which, keys_kind):
     y_obs = n - np.unique(b).size
     csr = expected_collisions(n, m) / y_obs
     assert 0.98 < csr < 1.02, csr
+
+
+def test_checksum_catches_one_wrong_output():
+    """The range checksum that the exhaustive GPU test compares: it equals
+    its definition written over the array form of the mixes, and one changed
+    output changes it."""
+    k = np.arange(4096, 8192, dtype=np.uint64)
+    h1 = oracle.bithash_many(1, k.astype(np.uint32)).astype(np.uint64)
+    h2 = oracle.bithash_many(2, k.astype(np.uint32)).astype(np.uint64)
+    acc = int(((h1 | (h2 << np.uint64(32))) * (2 * k + 1)).sum(dtype=np.uint64))
+    assert acc == oracle.bithash_checksum(4096, 8192)
+    h1[1000] ^= np.uint64(1 << 7)
+    bad = int(((h1 | (h2 << np.uint64(32))) * (2 * k + 1)).sum(dtype=np.uint64))
+    assert bad != acc

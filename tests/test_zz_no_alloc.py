@@ -15,6 +15,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+import oracle
 from paper_2510_15095_gb300 import workload as W
 
 torch = pytest.importorskip("torch")
@@ -69,3 +70,37 @@ def test_noalloc_rejects_oversize_and_resizable(H):
     assert t.size() == 0 and r.size() == 0
     t.close()
     r.close()
+
+
+def test_noalloc_against_the_oracle_up_to_full(H):
+    """The allocation-free insert against the oracle dictionary directly, on
+    a small fixed table driven past its capacity: every status (FULL
+    included) and every find must be the dictionary's outcome, with the FULL
+    ops left out.  Which ops get FULL depends on the layout, so the check is
+    that the outcome is valid: the stored keys are exactly the non-FULL ones
+    and at most slots + stash words are stored."""
+    slots = 1 << 10
+    n = 3000
+    keys, _ = W.take_keys(37, 0, n)
+    vals = W.values_for(keys, 37)
+    t = H.HiveTable(slots, stash_permille=0)  # stash floor of 1024 words
+    st = t.insert_noalloc(H.to_device_u32(keys), H.to_device_u32(vals)).cpu().numpy()
+    full = st == H.FULL
+    assert set(np.unique(st)) <= {H.INSERTED, H.FULL}
+    assert full.sum() >= n - (slots + 1024) and full.sum() > 0
+    d = oracle.Dict()
+    assert (d.insert(keys[~full], vals[~full]) == H.INSERTED).all()
+    v, f = t.find(H.to_device_u32(keys))
+    ev, ef = d.find(keys)
+    assert np.array_equal(H.to_host_u32(v), ev) and np.array_equal(f.cpu().numpy(), ef)
+    assert t.size() == len(d)
+    assert t.check() == 4  # HIVE_ERR_FULL, then cleared
+    # a second call re-inserts the kept keys with new values: all REPLACED
+    kept = keys[~full]
+    nv = W.values_for(kept, 38)
+    st2 = t.insert_noalloc(H.to_device_u32(kept), H.to_device_u32(nv)).cpu().numpy()
+    assert np.array_equal(st2, d.insert(kept, nv))
+    v, f = t.find(H.to_device_u32(keys))
+    ev, ef = d.find(keys)
+    assert np.array_equal(H.to_host_u32(v), ev) and np.array_equal(f.cpu().numpy(), ef)
+    t.close()
