@@ -62,9 +62,16 @@ def parse_args():
     ap.add_argument("--no-resize", action="store_true", help="skip the resize-stream leg")
     ap.add_argument("--bucket-slots", type=int, choices=[16, 32], default=0,
                     help="fix the bucket width instead of autotuning it (profiling runs)")
+    ap.add_argument("--l2-persist", type=int, choices=[-1, 0, 1], default=-1,
+                    help="fix the persisting L2 window of the free masks (-1: autotuned)")
+    ap.add_argument("--block-threads", type=int, choices=[0, 128, 256, 512], default=0,
+                    help="fix the bulk kernels' block shape (0: autotuned)")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the load-factor sweep and the L2-resident small-table leg")
     ap.add_argument("--resize-batches", type=int, default=32)
+    ap.add_argument("--resize-full", action="store_true",
+                    help="the whole resize trajectory: 159 growth + 159 shrink batches of 2^22 "
+                         "ops, 2^20 -> about 2^27 live keys and back (several minutes)")
     ap.add_argument("--tables-n", type=int, default=1024)
     ap.add_argument("--tables-steps", type=int, default=8)
     ap.add_argument("--serving-requests", type=int, default=3000)
@@ -323,7 +330,10 @@ def tables_leg(torch, H, dev, n_tables=1024, steps=8, seed=40):
     mixed batch of log-uniform [2^6, 2^20] ops (insert:find:erase 2:1:1).
     The same steps run once as one multi-table batch per step (CUDA graph
     replay) and once as one hive_execute per table per step, on two equal sets
-    of tables; outputs must be identical."""
+    of tables; outputs must be identical.  The same two arms also run on
+    fixed-capacity tables sized for every insert of the run: a fixed table's
+    hive_execute never waits for the GPU, so that plain arm measures launch
+    cost without the resizable arm's per-call size read-back."""
     from paper_2510_15095_gb300 import autotune as AT
     from paper_2510_15095_gb300 import workload as W
     rng = np.random.default_rng(seed)
@@ -338,11 +348,14 @@ def tables_leg(torch, H, dev, n_tables=1024, steps=8, seed=40):
     ins_total = nops.sum(axis=0) // 2
     max_slots = caps + (ins_total * 10 // 9) + caps // 2 + 64 * K
     sets = []
-    for _ in range(2):
+    for arm in range(4):  # resizable batched, resizable plain, fixed batched, fixed plain
         tabs = []
         for t in range(n_tables):
-            tb = H.HiveTable(int(caps[t]), max_slots=int(max_slots[t]), resizable=True,
-                             resize_batch=K, **knobs)
+            if arm < 2:
+                tb = H.HiveTable(int(caps[t]), max_slots=int(max_slots[t]), resizable=True,
+                                 resize_batch=K, **knobs)
+            else:
+                tb = H.HiveTable(int(max_slots[t]), **knobs)
             k, v = W.preload_t(torch, 7000 + t, int(caps[t]) // 2, dev)
             tb.insert(k, v, status=False)
             tabs.append(tb)
@@ -359,28 +372,54 @@ def tables_leg(torch, H, dev, n_tables=1024, steps=8, seed=40):
     outs = [[(torch.empty(w[1].numel(), dtype=torch.int32, device=dev),
               torch.empty(w[1].numel(), dtype=torch.uint8, device=dev)) for w in row] for row in work]
     max_ops = int(nops.sum(axis=1).max()) + 1
-    multi = H.HiveMulti(sets[0], max_segments=n_tables, max_ops=max_ops, use_graph=True)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for st in range(steps):
-        multi.execute([{"table": t, "ops": w[0], "keys": w[1], "vals": w[2], "n_insert": w[3],
-                        "vals_out": outs[st][t][0], "status": outs[st][t][1]}
-                       for t, w in enumerate(work[st])])
-    torch.cuda.synchronize(dev)
-    t_multi = time.perf_counter() - t0
-    plain_out = []
-    t0 = time.perf_counter()
-    for st in range(steps):
-        for t, w in enumerate(work[st]):
-            plain_out.append(sets[1][t].execute(w[0], w[1], w[2]))
-    torch.cuda.synchronize(dev)
-    t_plain = time.perf_counter() - t0
-    same = all(torch.equal(outs[st][t][0], plain_out[st * n_tables + t][0]) and
-               torch.equal(outs[st][t][1], plain_out[st * n_tables + t][1])
-               for st in range(steps) for t in range(n_tables))
-    caps_same = all(a.capacity() == b.capacity() for a, b in zip(*sets))
+
+    def batched(tabs, out):
+        multi = H.HiveMulti(tabs, max_segments=n_tables, max_ops=max_ops, use_graph=True)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for st in range(steps):
+            multi.execute([{"table": t, "ops": w[0], "keys": w[1], "vals": w[2], "n_insert": w[3],
+                            "vals_out": out[st][t][0], "status": out[st][t][1]}
+                           for t, w in enumerate(work[st])])
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        multi.close()
+        return dt
+
+    def plain(tabs):
+        res = []
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for st in range(steps):
+            for t, w in enumerate(work[st]):
+                res.append(tabs[t].execute(w[0], w[1], w[2]))
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0, res
+
+    p0 = sum(tb.stats()["probes"] for tb in sets[0])
+    c0 = sum(tb.stats()["claimed_fast"] + tb.stats()["claimed_slow"] for tb in sets[0])
+    t_multi = batched(sets[0], outs)
+    probes = sum(tb.stats()["probes"] for tb in sets[0]) - p0
+    claims = sum(tb.stats()["claimed_fast"] + tb.stats()["claimed_slow"] for tb in sets[0]) - c0
+    t_plain, plain_out = plain(sets[1])
+    outs_fixed = [[(torch.empty_like(o[0]), torch.empty_like(o[1])) for o in row] for row in outs]
+    t_multi_fixed = batched(sets[2], outs_fixed)
+    t_plain_fixed, plain_fixed_out = plain(sets[3])
+
+    def same_as(res):
+        return all(torch.equal(outs[st][t][0], res[st * n_tables + t][0]) and
+                   torch.equal(outs[st][t][1], res[st * n_tables + t][1])
+                   for st in range(steps) for t in range(n_tables))
+    same = same_as(plain_out) and same_as(plain_fixed_out) and all(
+        torch.equal(outs[st][t][i], outs_fixed[st][t][i])
+        for st in range(steps) for t in range(n_tables) for i in range(2))
+    caps_same = all(a.capacity() == b.capacity() for a, b in zip(sets[0], sets[1]))
     ops_total = int(nops.sum())
-    multi.close()
+    # step-level algorithmic bytes of the batched resizable arm (op I/O, every
+    # probed bucket, a written sector per claimed slot) over its wall time
+    S = knobs["bucket_slots"]
+    byts = 14 * ops_total + 8 * S * probes + 32 * claims
+    peak_gbs, peak_kind = measured_peak()
     for tabs in sets:
         for tb in tabs:
             tb.close()
@@ -389,7 +428,17 @@ def tables_leg(torch, H, dev, n_tables=1024, steps=8, seed=40):
                          "(insert:find:erase 2:1:1)"),
             "ops": ops_total, "batched_gops": ops_total / t_multi / 1e9,
             "plain_gops": ops_total / t_plain / 1e9, "speedup": t_plain / t_multi,
-            "batched_s": t_multi, "plain_s": t_plain, "identical_results": bool(same),
+            "batched_s": t_multi, "plain_s": t_plain,
+            "fixed_tables": {"batched_gops": ops_total / t_multi_fixed / 1e9,
+                             "plain_gops": ops_total / t_plain_fixed / 1e9,
+                             "speedup": t_plain_fixed / t_multi_fixed},
+            "roofline": {"bound": "hbm", "algorithmic_bytes": byts,
+                         "achieved": byts / t_multi / 1e9, "peak": peak_gbs, "unit": "GB/s",
+                         "frac": byts / t_multi / 1e9 / peak_gbs, "peak_source": peak_kind,
+                         "probes_per_op": probes / ops_total,
+                         "note": "batched resizable arm, whole steps by host wall clock; most "
+                                 "of the 1024 tables fit in L2"},
+            "identical_results": bool(same),
             "identical_capacity": bool(caps_same), "graph": True,
             "tuned": {"resize_batch": K, **knobs}}
 
@@ -604,11 +653,15 @@ def plain_leg(torch, H, dev, seed=80, reps=5):
                     a32[torch.randint(0, n_find, (n_find,), generator=g, device=dev)])
     er = k32[torch.randperm(n_ins, generator=g, device=dev)[: n_ins // 2]]
     t = H.HiveTable(slots)
+    S = int(t.config.bucket_slots)
     st = torch.empty(n_ins, dtype=torch.uint8, device=dev)
     fv = torch.empty(n_find, dtype=torch.int32, device=dev)
     ff = torch.empty(n_find, dtype=torch.uint8, device=dev)
     es = torch.empty(n_ins // 2, dtype=torch.uint8, device=dev)
     ins_ms = _median_ms(torch, stream, dev, lambda: t.insert(k32, v32, status=st), reps, setup=t.clear)
+    p0 = t.stats()["probes"]
+    t.find(q, vals_out=fv, found=ff)
+    find_probes = t.stats()["probes"] - p0
     f1_ms = _median_ms(torch, stream, dev, lambda: t.find(q, vals_out=fv, found=ff), reps)
     assert bool(((ff == 1) == hit).all())
 
@@ -624,7 +677,12 @@ def plain_leg(torch, H, dev, seed=80, reps=5):
                          "(half absent), erase 419,430, find again"),
             "insert_gops": n_ins / ins_ms / 1e6, "find_gops": n_find / f1_ms / 1e6,
             "erase_gops": (n_ins // 2) / er_ms / 1e6, "find_after_erase_gops": n_find / f2_ms / 1e6,
-            "ms": {"insert": ins_ms, "find": f1_ms, "erase": er_ms, "find_after_erase": f2_ms}}
+            "ms": {"insert": ins_ms, "find": f1_ms, "erase": er_ms, "find_after_erase": f2_ms},
+            # bytes served from L2: each insert probes both buckets, each find
+            # the buckets it reads (counted by the kernel), plus the op I/O
+            "achieved_l2_gbs": {"insert": (9 + 2 * 8 * S + 32) * n_ins / ins_ms / 1e6,
+                                "find": (9 * n_find + 8 * S * find_probes) / f1_ms / 1e6},
+            "find_probes_per_op": find_probes / n_find}
 
 
 # ---------------------------------------------------------------------------
@@ -635,11 +693,18 @@ def resize_leg(torch, H, dev, batches=32, n_batch=1 << 22, seed=60):
     """One resizable table starting with 2^20 live keys; `batches` growth
     batches of 2^22 ops (insert:erase:find 40/20/40) then as many shrink
     batches (20/40/40), finds Zipf(0.99) over live keys, thresholds 0.9/0.4,
-    K = 1024.  Also times single split and merge launches of 32,768 bucket
-    pairs (the size the paper reports resize throughput on)."""
+    K = 1024.  159 + 159 batches is the whole trajectory to 2^27 live keys
+    and back.  The op-weighted roofline counts each op's probed buckets and
+    I/O and each split or merge's bucket reads and writes.  At the end a
+    sample of live keys must be found with their values and a sample of
+    erased ones must not.  Also times single split and merge launches of
+    32,768 bucket pairs (the size the paper reports resize throughput on)."""
     from paper_2510_15095_gb300 import workload as W
     start = 1 << 20
-    t = H.HiveTable(1 << 21, max_slots=1 << 27, resizable=True, resize_batch=1024, shrink=(2, 5))
+    peak_est = start + batches * (n_batch // 5)
+    max_slots = 1 << max(27, int(peak_est * 10 // 9 + 1).bit_length())
+    t = H.HiveTable(1 << 21, max_slots=max_slots, resizable=True, resize_batch=1024, shrink=(2, 5))
+    S = int(t.config.bucket_slots)
     k, v = W.preload_t(torch, seed, start, dev)
     t.insert(k, v, status=False)
     live = torch.arange(start, dtype=torch.int64, device=dev)
@@ -655,6 +720,8 @@ def resize_leg(torch, H, dev, batches=32, n_batch=1 << 22, seed=60):
     out = {}
     t.profile(True)
     t.profile_read()
+    s0 = t.stats()
+    t_total = 0.0
     for phase in ("grow", "shrink"):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -662,12 +729,47 @@ def resize_leg(torch, H, dev, batches=32, n_batch=1 << 22, seed=60):
             t.execute(*w)
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
+        t_total += dt
         out[f"{phase}_gops"] = batches * n_batch / dt / 1e9
         out[f"{phase}_capacity_slots"] = t.capacity()
     prof = t.profile_read()
     t.profile(False)
     st = t.stats()
     size_end = t.size()
+    # op-weighted algorithmic bytes: op I/O (op code, key, value in; value,
+    # status out), every probed bucket, a written sector per claimed slot,
+    # and per split or merge pair one bucket read and two written
+    n_ops = 2 * batches * n_batch
+    probes = st["probes"] - s0["probes"]
+    claims = (st["claimed_fast"] - s0["claimed_fast"]) + (st["claimed_slow"] - s0["claimed_slow"])
+    pairs = (st["splits"] - s0["splits"]) + (st["merges"] - s0["merges"])
+    byts = 14 * n_ops + 8 * S * probes + 32 * claims + 3 * 8 * S * pairs
+    peak_gbs, peak_kind = measured_peak()
+    ach = byts / t_total / 1e9
+    out["roofline"] = {"bound": "hbm", "algorithmic_bytes": byts, "achieved": ach,
+                       "peak": peak_gbs, "unit": "GB/s", "frac": ach / peak_gbs,
+                       "peak_source": peak_kind, "probes_per_op": probes / n_ops,
+                       "note": "whole stream by host wall clock, resize launches included"}
+    # properties at the end: live keys found with their values, erased keys not
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed + 5)
+    dead = torch.ones(ctr, dtype=torch.bool, device=dev)
+    dead[live] = False
+    dead_pos = torch.nonzero(dead).flatten()
+    nsamp = min(1 << 20, int(live.numel()), int(dead_pos.numel()))
+    lp = live[torch.randint(0, live.numel(), (nsamp,), generator=g, device=dev)]
+    dp = dead_pos[torch.randint(0, dead_pos.numel(), (nsamp,), generator=g, device=dev)]
+    to32 = lambda x: (x - ((x >> 31) << 32)).to(torch.int32)  # noqa: E731
+    lk = W.feistel_bits_t(lp, seed, 32)
+    lk = lk[lk < 0xFFFFFFFE]  # a reserved key is never stored
+    fv, ff = t.find(to32(lk))
+    ok_live = bool((ff == 1).all()) and bool(torch.equal(fv, to32(W.splitmix32_t(lk ^ seed))))
+    _, fd = t.find(to32(W.feistel_bits_t(dp, seed, 32)))
+    ok_dead = bool((fd == 0).all())
+    n_live = int((W.feistel_bits_t(live, seed, 32) < 0xFFFFFFFE).sum())
+    assert ok_live and ok_dead and size_end == n_live, "resize stream lost keys"
+    out["sample_check"] = {"live_found": ok_live, "erased_absent": ok_dead, "sample": nsamp,
+                           "size_matches_generator": size_end == n_live}
     t.close()
     # split / merge launches of 32,768 pairs on a table of 32,768 buckets
     m = H.HiveTable(1 << 20, max_slots=1 << 22, resizable=True, resize_batch=32768, shrink=(2, 5))
@@ -686,7 +788,7 @@ def resize_leg(torch, H, dev, batches=32, n_batch=1 << 22, seed=60):
     out.update({
         "workload": (f"one resizable table from 2^20 live keys, {batches} growth + {batches} shrink "
                      "batches of 2^22 ops (40/20/40 then 20/40/40 insert:erase:find, Zipf 0.99 "
-                     "finds), thresholds 0.9 / 0.4, K = 1024"),
+                     f"finds), thresholds 0.9 / 0.4, K = 1024, growth limit {max_slots} slots"),
         "peak_live_keys": peak, "end_live_keys": size_end,
         "splits": st["splits"], "merges": st["merges"],
         "kernel_ms": {kk: vv[0] for kk, vv in prof.items()},
@@ -863,6 +965,10 @@ def main():
         tuned = {"bucket_slots": args.bucket_slots, "max_evictions": 16, "placement": 0}
     else:
         tuned = AT.tune(args.slots, 95, (1, 2, 1), False, space=BENCH_SPACE)
+    if args.l2_persist >= 0:
+        tuned["l2_persist"] = args.l2_persist
+    if args.block_threads:
+        tuned["block_threads"] = args.block_threads
     cfg["table"] = dict(tuned)
     t = H.HiveTable(args.slots, **tuned)
     stream = torch.cuda.current_stream(dev)
@@ -1050,7 +1156,8 @@ def main():
     if not args.no_serving:
         extra["serving"] = serving_leg(torch, H, dev, n_requests=args.serving_requests)
     if not args.no_resize:
-        extra["resize_stream"] = resize_leg(torch, H, dev, batches=args.resize_batches)
+        extra["resize_stream"] = resize_leg(torch, H, dev,
+                                           batches=159 if args.resize_full else args.resize_batches)
     if not args.no_sweep:
         extra["load_sweep"] = sweep_leg(torch, H, dev, tuned, slots=args.slots,
                                         n_find=N_FIND if args.slots == SLOTS else args.slots)

@@ -1549,8 +1549,11 @@ __device__ __forceinline__ void overflow_item(const View& v, uint64_t word0, uin
   }
 }
 
+#ifndef HIVE_OVF_MIN_BLOCKS
+#define HIVE_OVF_MIN_BLOCKS 1  // resident blocks per SM the eviction kernel's registers allow
+#endif
 template <int S>
-__global__ void __launch_bounds__(kOvfThreads)
+__global__ void __launch_bounds__(kOvfThreads, HIVE_OVF_MIN_BLOCKS)
     k_overflow(View v, List in, List pend, int resizable, uint8_t* __restrict__ status) {
   // one item per group of S lanes at a time
   const int lane = threadIdx.x & 31;
@@ -1765,6 +1768,11 @@ __device__ __forceinline__ void run_chunk_fused(const View& v, uint32_t stash_n,
   uint32_t outv = 0;
   uint32_t f1 = 0, s1 = S, f2 = 0, s2 = S;
   bool absent = false;  // a miss that survived the version check
+  // The first probe of a find or erase is optimistic: it reads no versions,
+  // since a hit needs no check (the word was seen in place).  A miss then
+  // probes again under the version check.  Inserts, which mostly miss (new
+  // keys), take the checked probe from the start.
+  bool checked = op == OP_INSERT;
   for (uint32_t attempt = 0;; ++attempt) {
     const bool active = !done && !absent;
     unsigned need = __ballot_sync(kFull, active);
@@ -1773,12 +1781,15 @@ __device__ __forceinline__ void run_chunk_fused(const View& v, uint32_t stash_n,
       if (lane == 0) atomicOr(&v.ctrl->err, kErrTimeout);
       break;
     }
+    const bool unchecked_miss = attempt == 1 && active && !checked;
     if (attempt) {
-      retries += (lane == 0) ? __popc(need) : 0u;
-      __nanosleep(64u << min(attempt, 6u));
+      const unsigned rep = __ballot_sync(kFull, active && !unchecked_miss);
+      retries += (lane == 0) ? __popc(rep) : 0u;
+      if (rep) __nanosleep(64u << min(attempt, 6u));
+      checked = true;
     }
     uint32_t v1 = 0, v2 = 0;
-    if (active) {
+    if (active && checked) {
       v1 = ld_acquire32(v.vers + b1);
       v2 = ld_acquire32(v.vers + b2);
     }
@@ -1836,7 +1847,7 @@ __device__ __forceinline__ void run_chunk_fused(const View& v, uint32_t stash_n,
         }
       }
     }
-    if (active && !done && !retry) {
+    if (active && !done && !retry && checked) {
       __threadfence();
       const uint32_t w1 = ld_acquire32(v.vers + b1);
       const uint32_t w2 = ld_acquire32(v.vers + b2);
