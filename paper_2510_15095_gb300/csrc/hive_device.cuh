@@ -27,8 +27,10 @@ enum : uint32_t { OP_INSERT = 0, OP_FIND = 1, OP_ERASE = 2 };
 // Hashing and addressing
 // ----------------------------------------------------------------------------
 
-// BitHash1 (Section III-C, Listing 1) without the final reduction: a
-// Wang-style shift/xor/multiply avalanche.
+// BitHash1 of Section III-C without the final reduction: Thomas Wang's
+// 32-bit integer hash (the variant of his shift/xor/multiply avalanche that
+// starts with (k << 15) - k - 1 and multiplies by 2057 = 1 + 2^3 + 2^11 near
+// the end), a bijection of 32-bit words.
 __device__ __forceinline__ uint32_t bithash1(uint32_t k) {
   uint32_t x = (k << 15) - k - 1u;
   x = x ^ (x >> 12);
@@ -38,8 +40,10 @@ __device__ __forceinline__ uint32_t bithash1(uint32_t k) {
   return x ^ (x >> 16);
 }
 
-// BitHash2 (Section III-C, Listing 1) without the final reduction: Jenkins'
-// six-step add/xor/shift mix.
+// BitHash2 of Section III-C without the final reduction: Bob Jenkins'
+// six-step 32-bit integer hash, alternating an add of a constant with a
+// shift, then an xor with a constant with a shift; each add of a shifted
+// copy is the multiplication by 1 + 2^s it equals.
 __device__ __forceinline__ uint32_t bithash2(uint32_t k) {
   uint32_t x = k * 4097u + 0x7ED55D16u;
   x = x ^ (x >> 19) ^ 0xC761C23Cu;
