@@ -1017,6 +1017,7 @@ def main():
     probes_find = s_find["probes"] - s_ins["probes"]
     probes_mix = s_mix["probes"] - s_find["probes"]
     claimed_mix = s_mix["claimed_fast"] - s_find["claimed_fast"]
+    overflowed_mix = s_mix["overflowed"] - s_find["overflowed"]
     overflowed = s_ins["overflowed"]
     stashed = s_ins["stashed"]
 
@@ -1049,16 +1050,25 @@ def main():
     ins_ms = prof.get("insert", (0.0, 1))
     find_ms = prof.get("find", (0.0, 1))
     mix_ms = prof.get("mixed", (0.0, 1))
-    # mixed I/O: op, key, value in; value, status out
+    claim_ms = prof.get("claim", (0.0, 1))
+    # mixed I/O: op, key, value in; value, status out.  A batch of 2^18 ops or
+    # more claims its new keys in the claim kernel, whose bytes are its own:
+    # a 12-byte list entry and a status byte per new key, a written sector
+    # per claim (the free masks it reads are served by L2)
     bb = 8 * int(tuned.get("bucket_slots", 32))  # bytes per bucket probe
-    bytes_mix = 14 * n_mix + bb * probes_mix + 32 * claimed_mix
+    deferred = claim_ms[1] > 0
+    bytes_mix = 14 * n_mix + bb * probes_mix + (0 if deferred else 32 * claimed_mix)
+    bytes_claim = 13 * (claimed_mix + overflowed_mix) + 32 * claimed_mix
     bytes_find = 9 * n_find + bb * probes_find  # key in, value + flag out, probed buckets
     bytes_ins = 9 * n_ins + bb * probes_ins + 32 * (n_ins - overflowed)  # + one written sector
     rl = {}
     sw = int(tuned.get("bucket_slots", 32))
     for name, (tot, cnt), byts, kname in (("insert", ins_ms, bytes_ins, f"k_ops<insert,S={sw}>"),
                                             ("find", find_ms, bytes_find, f"k_ops<find,S={sw}>"),
-                                            ("mixed", mix_ms, bytes_mix, f"k_ops<mixed,S={sw}>")):
+                                            ("mixed", mix_ms, bytes_mix, f"k_ops<mixed,S={sw}>"),
+                                            ("claim", claim_ms, bytes_claim, f"k_claim<S={sw}>")):
+        if name == "claim" and not deferred:
+            continue
         avg = tot / max(cnt, 1)
         ach = byts / (avg / 1e3) / 1e9 if avg > 0 else 0.0
         traffic, _ = recorded_traffic(kname)
