@@ -75,6 +75,10 @@ def parse_args():
     ap.add_argument("--tables-n", type=int, default=1024)
     ap.add_argument("--tables-steps", type=int, default=8)
     ap.add_argument("--serving-requests", type=int, default=3000)
+    ap.add_argument("--serving-preload-log2", type=int, default=22,
+                    help="keys preloaded into each of the 64 served tables (log2)")
+    ap.add_argument("--serving-max-log2", type=int, default=25,
+                    help="growth limit of each served table in slots (log2)")
     return ap.parse_args()
 
 
@@ -1164,7 +1168,9 @@ def main():
         extra["multi_table"] = tables_leg(torch, H, dev, n_tables=args.tables_n,
                                           steps=args.tables_steps)
     if not args.no_serving:
-        extra["serving"] = serving_leg(torch, H, dev, n_requests=args.serving_requests)
+        extra["serving"] = serving_leg(torch, H, dev, n_requests=args.serving_requests,
+                                       preload_log2=args.serving_preload_log2,
+                                       max_slots_log2=args.serving_max_log2)
     if not args.no_resize:
         extra["resize_stream"] = resize_leg(torch, H, dev,
                                            batches=159 if args.resize_full else args.resize_batches)
