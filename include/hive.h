@@ -295,14 +295,22 @@ hive_status hive_profile_enable(hive_table* t, int enable);
 hive_status hive_profile_read(hive_table* t, hive_profile_t* out);
 
 /* ---- Host-buffer calls ----
- * Same operations with the op arrays in HOST memory.  The batch streams
- * through device staging in chunks of 2^22 ops, two at a time, so that the
- * host-to-device copy of one chunk, the kernels of the previous one and the
- * copy back of the one before overlap (fully when the host buffers are pinned,
- * e.g. cudaMallocHost).  Results equal the device-pointer calls (chunking does
- * not change them under the batch contract).  The call returns when every
- * output is in host memory.  The staging (about 120 MB) is allocated on the
- * first host-buffer call of a table and freed by hive_destroy. */
+ * Same operations with the op arrays in HOST memory.  The call returns when
+ * every output is in host memory; results equal the device-pointer calls.
+ * Two ways through, picked per call:
+ *  - direct: when the current device reaches host memory coherently through
+ *    the CPU-GPU link (hive_host_direct_access reports 1; GB300's NVLink-C2C)
+ *    and every array is pinned or registered host memory (cudaMallocHost,
+ *    cudaHostRegister) or device memory, the kernels read the inputs and write
+ *    the results in place, with no staging copies;
+ *  - staged: otherwise (pageable arrays, other GPUs, or HIVE_HOSTIO_STAGED=1
+ *    in the environment) the batch streams through device staging in chunks
+ *    of 2^22 ops, two at a time, so that the host-to-device copy of one
+ *    chunk, the kernels of the previous one and the copy back of the one
+ *    before overlap (fully when the host buffers are pinned).  Chunking does
+ *    not change results under the batch contract.  The staging (about 120 MB)
+ *    is allocated on the first staged call of a table and freed by
+ *    hive_destroy. */
 hive_status hive_insert_host(hive_table* t, const uint32_t* h_keys, const uint32_t* h_vals,
                              uint64_t n, uint8_t* h_status, void* stream);
 hive_status hive_find_host(hive_table* t, const uint32_t* h_keys, uint64_t n,
@@ -310,6 +318,12 @@ hive_status hive_find_host(hive_table* t, const uint32_t* h_keys, uint64_t n,
 hive_status hive_execute_host(hive_table* t, const uint8_t* h_ops, const uint32_t* h_keys,
                               const uint32_t* h_vals, uint64_t n, uint32_t* h_vals_out,
                               uint8_t* h_status, void* stream);
+
+/* *out = 1 when the current device reaches host memory coherently through the
+ * CPU-GPU link (cudaDevAttrPageableMemoryAccessUsesHostPageTables), so that
+ * host-buffer calls on pinned or registered arrays take the direct way; else
+ * 0.  INVALID_ARG for NULL out; CUDA when the device cannot be queried. */
+hive_status hive_host_direct_access(int* out);
 
 /* ---- Multi-table batches (many independent tables, one launch per phase) ----
  * Not in the paper: the tables are the paper's, the batching is a library

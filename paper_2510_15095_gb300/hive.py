@@ -36,7 +36,8 @@ EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", 
            "hive32_config_default", "hive32_create", "hive32_destroy", "hive32_insert",
            "hive32_find", "hive32_erase", "hive32_execute", "hive32_size", "hive32_clear",
            "hive32_check",
-           "hive32_stats", "hive32_dump", "hive_debug_fail_alloc", "hive_debug_hold_lock", "hive_hash"]
+           "hive32_stats", "hive32_dump", "hive_debug_fail_alloc", "hive_debug_hold_lock", "hive_hash",
+           "hive_host_direct_access"]
 KERNEL_KINDS = ["find", "insert", "erase", "mixed", "evict", "maint", "split", "merge", "count",
                 "fused", "claim"]
 
@@ -156,6 +157,7 @@ def load_library(path: str = LIB_PATH):
         L.hive_debug_fail_alloc.argtypes = [C.c_uint32]
         L.hive_hash.argtypes = [vp, u64, vp, vp, vp]
         L.hive_debug_hold_lock.argtypes = [vp, u64, i32, vp]
+        L.hive_host_direct_access.argtypes = [vp]
         L.hive_last_error.argtypes = []
         L.hive_last_error.restype = C.c_char_p
         for name in EXPORTS:
@@ -332,7 +334,9 @@ class HiveTable:
         return t.data_ptr()
 
     def insert_host(self, keys, vals, status=None, stream=None):
-        """hive_insert_host: keys/vals (and status, if given) are CPU tensors."""
+        """hive_insert_host: keys/vals (and status, if given) are CPU tensors.
+        Pinned tensors run in place where host_direct_access() holds; pageable
+        ones stream through device staging."""
         n = keys.numel()
         _raise(self._L, self._L.hive_insert_host(
             self._h, self._hptr(keys, 4, n, "keys"), self._hptr(vals, 4, n, "vals"), n,
@@ -599,6 +603,15 @@ def hash_keys(keys, stream=None):
     _raise(L, L.hive_hash(_dptr(keys, 4, n, "keys"), n, _dptr(h1, 4, n, "h1"),
                           _dptr(h2, 4, n, "h2"), _stream_ptr(stream)))
     return h1, h2
+
+
+def host_direct_access() -> bool:
+    """hive_host_direct_access: whether the current device reaches host memory
+    coherently, so that host-buffer calls on pinned arrays run in place."""
+    L = load_library()
+    out = C.c_int(0)
+    _raise(L, L.hive_host_direct_access(C.byref(out)))
+    return bool(out.value)
 
 
 def debug_fail_alloc(n: int):

@@ -169,10 +169,11 @@ def test_allocation_failure_returns_oom(H):
     # the same call succeeds once the allocations do
     assert np.array_equal(t.insert(up(H, big), up(H, bvals)).cpu().numpy(), d.insert(big, bvals))
     check_find(H, t, d, np.concatenate([keys, big]))
-    # host-buffer calls allocate their device staging on first use
-    hk = torch.from_numpy(keys.view(np.int32)).pin_memory()
-    hv = torch.empty(keys.size, dtype=torch.int32).pin_memory()
-    hf = torch.empty(keys.size, dtype=torch.uint8).pin_memory()
+    # staged host-buffer calls (pageable arrays) allocate their device
+    # staging on first use
+    hk = torch.from_numpy(keys.view(np.int32).copy())
+    hv = torch.empty(keys.size, dtype=torch.int32)
+    hf = torch.empty(keys.size, dtype=torch.uint8)
     H.debug_fail_alloc(2)
     with pytest.raises(H.HiveError) as e:
         t.find_host(hk, hv, hf)

@@ -325,10 +325,16 @@ def test_2e26_slots_95pct_load(H, bs):
     t.close()
 
 
-def test_host_buffer_calls_match_device_calls(H):
-    """hive_*_host stream pinned host arrays through device staging in chunks
-    of 2^22 ops; with 5 million ops (two full slots and a ragged tail) the
-    results must equal the device-pointer calls bit for bit."""
+@pytest.mark.parametrize("way", ["direct", "staged"])
+def test_host_buffer_calls_match_device_calls(H, way, monkeypatch):
+    """hive_*_host on host arrays: with pinned arrays on a GPU with coherent
+    host access the kernels work on them in place ("direct"); with
+    HIVE_HOSTIO_STAGED=1 they stream through device staging in chunks of
+    2^22 ops ("staged").  With 5 million ops (two full chunks and a ragged
+    tail) the results must equal the device-pointer calls bit for bit; the
+    mixed batch uses pageable buffers, which always take the staged way."""
+    if way == "staged":
+        monkeypatch.setenv("HIVE_HOSTIO_STAGED", "1")
     n = 5_000_000
     keys, c = W.take_keys(41, 0, n)
     vals = W.values_for(keys, 41)
@@ -346,18 +352,39 @@ def test_host_buffer_calls_match_device_calls(H):
     hq = torch.from_numpy(q.view(np.int32)).pin_memory()
     vb = torch.empty(q.size, dtype=torch.int32).pin_memory()
     fb = torch.empty(q.size, dtype=torch.uint8).pin_memory()
-    b.find_host(hq, vb, fb)
+    if way == "direct" and H.host_direct_access():
+        # in place: the table has no staging yet and this call allocates none,
+        # so a failing allocation is not met
+        H.debug_fail_alloc(1)
+    try:
+        b.find_host(hq, vb, fb)
+    finally:
+        H.debug_fail_alloc(0)
     assert torch.equal(va.cpu(), vb) and torch.equal(fa.cpu(), fb)
+    # found flags may be left out
+    vb2 = torch.empty(q.size, dtype=torch.int32).pin_memory()
+    b.find_host(hq, vb2)
+    assert torch.equal(vb, vb2)
     rng = np.random.default_rng(4)
     new, _ = W.take_keys(41, c + n, 100_000)
     ops, mk, mv = W.mixed_batch(rng, keys, new, 100_000, 100_000, 300_000, seed=41)
     vo_a, st_a = a.execute(torch.from_numpy(ops).cuda(), up(H, mk), up(H, mv))
     vo_b = torch.empty(ops.size, dtype=torch.int32)
-    st_b = torch.empty(ops.size, dtype=torch.uint8)  # pageable buffers work too
+    st_b = torch.empty(ops.size, dtype=torch.uint8)  # pageable
     b.execute_host(torch.from_numpy(ops), torch.from_numpy(mk.view(np.int32)),
                    torch.from_numpy(mv.view(np.int32)), vo_b, st_b)
     assert torch.equal(vo_a.cpu(), vo_b) and torch.equal(st_a.cpu(), st_b)
+    # the same mixed batch shape again, pinned, on both tables
+    ops2, mk2, mv2 = W.mixed_batch(rng, keys, new, 50_000, 100_000, 200_000, seed=42)
+    vo_a, st_a = a.execute(torch.from_numpy(ops2).cuda(), up(H, mk2), up(H, mv2))
+    vo_b = torch.empty(ops2.size, dtype=torch.int32).pin_memory()
+    st_b = torch.empty(ops2.size, dtype=torch.uint8).pin_memory()
+    b.execute_host(torch.from_numpy(ops2).pin_memory(),
+                   torch.from_numpy(mk2.view(np.int32)).pin_memory(),
+                   torch.from_numpy(mv2.view(np.int32)).pin_memory(), vo_b, st_b)
+    assert torch.equal(vo_a.cpu(), vo_b) and torch.equal(st_a.cpu(), st_b)
     assert a.size() == b.size()
+    assert a.check() == 0 and b.check() == 0
     a.close()
     b.close()
 
