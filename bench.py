@@ -66,6 +66,8 @@ def parse_args():
                     help="fix the persisting L2 window of the free masks (-1: autotuned)")
     ap.add_argument("--block-threads", type=int, choices=[0, 128, 256, 512], default=0,
                     help="fix the bulk kernels' block shape (0: autotuned)")
+    ap.add_argument("--no-breakdown", action="store_true",
+                    help="skip the insertion-step breakdown against load factor")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the load-factor sweep and the L2-resident small-table leg")
     ap.add_argument("--resize-batches", type=int, default=32)
@@ -638,6 +640,82 @@ def sweep_leg(torch, H, dev, table_kw, slots=SLOTS, n_find=N_FIND, seed=70, reps
     return out
 
 
+BREAKDOWN_LOADS = (55, 65, 75, 85, 90, 93, 95, 97)
+STEP_STATS = ("replaced", "claimed_fast", "overflowed", "claimed_slow", "evict_rounds",
+              "lock_acquired", "lock_timeouts", "stashed", "pending", "stash_reinserted")
+
+
+def breakdown_leg(torch, H, dev, table_kw, slots=SLOTS, seed=75, reps=3):
+    """Insertion-step breakdown against load factor (the paper's Section V-D
+    analysis, over loads 0.55-0.97).  For each load, a fresh bulk fill of an
+    empty fixed table to that load ("fill") and the last 5% of the fill alone
+    ("window", from load - 5% on), each timed per kernel with the profiling
+    hook's CUDA events and counted per step with the table's counters:
+
+    - steps 1-2 (replace, claim) run in the bulk kernel;
+    - step 3 (bounded eviction) is the eviction kernel, which also appends
+      the words of chains that gave up to the stash (one atomic each);
+    - step 4 (stash) is that append plus the maintenance kernel.
+
+    The phased design runs each step as its own kernel, so the shares are
+    kernel times, where the paper sums per-step clock counts inside one
+    kernel."""
+    from paper_2510_15095_gb300 import workload as W
+    stream = torch.cuda.current_stream(dev)
+    n_max = (slots * BREAKDOWN_LOADS[-1] + 50) // 100
+    k = _valid_keys_t(torch, W, seed, 0, n_max, dev)
+    v = W.splitmix32_t(k ^ seed)
+    k32, v32 = _i32(torch, k), _i32(torch, v)
+    st = torch.empty(n_max, dtype=torch.uint8, device=dev)
+    t = H.HiveTable(slots, **table_kw)
+    out = {"workload": (f"fixed table of {slots} slots; fresh bulk fills to each load and the "
+                        f"last 5% of each fill alone; uniform unique u32 keys"),
+           "table": dict(table_kw), "loads": {}}
+    kinds = {"steps_1_2": ("insert",), "step_3": ("evict",), "step_4": ("maint",)}
+
+    def one(lo, hi):
+        def setup():
+            t.clear()
+            if lo:
+                t.insert(k32[:lo], v32[:lo], status=False)
+        runs = []
+        for _ in range(reps):
+            setup()
+            torch.cuda.synchronize(dev)
+            before = t.stats()
+            t.profile(True)
+            t.profile_read()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t.insert(k32[lo:hi], v32[lo:hi], status=st[lo:hi])
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            prof = t.profile_read()
+            t.profile(False)
+            after = t.stats()
+            runs.append((e0.elapsed_time(e1), prof, {f: after[f] - before[f] for f in STEP_STATS}))
+        runs.sort(key=lambda r: r[0])
+        ms, prof, cnt = runs[len(runs) // 2]
+        n = hi - lo
+        steps = {name: sum(prof.get(kk, (0.0, 0))[0] for kk in ks) for name, ks in kinds.items()}
+        tot = sum(steps.values()) or 1.0
+        inserted = int((st[lo:hi] == H.INSERTED).sum().item())
+        code = t.check()
+        return {"n_insert": n, "ms": ms, "gops": n / ms / 1e6,
+                "kernel_ms": {kk: round(vv, 4) for kk, vv in steps.items()},
+                "share": {kk: round(vv / tot, 5) for kk, vv in steps.items()},
+                "counts": cnt, "lock_fraction": cnt["lock_acquired"] / n,
+                "inserted": inserted, "check": code}
+
+    for L in BREAKDOWN_LOADS:
+        hi = (slots * L + 50) // 100
+        lo = (slots * (L - 5) + 50) // 100
+        out["loads"][str(L)] = {"fill": one(0, hi), "window": one(lo, hi)}
+    t.close()
+    return out
+
+
 def plain_leg(torch, H, dev, seed=80, reps=5):
     """The small plain table (2^20 slots, 8 MiB, resident in the 129 MB L2):
     insert 838,861 keys (80%), 1,677,722 finds (half absent), erase a seeded
@@ -1195,6 +1273,11 @@ def main():
     if not args.no_resize:
         extra["resize_stream"] = resize_leg(torch, H, dev,
                                            batches=159 if args.resize_full else args.resize_batches)
+    if not args.no_breakdown:
+        extra["insert_breakdown"] = {
+            "tuned": breakdown_leg(torch, H, dev, tuned, slots=args.slots),
+            "paper_s32": breakdown_leg(torch, H, dev, dict(tuned, bucket_slots=32),
+                                       slots=args.slots)}
     if not args.no_sweep:
         extra["load_sweep"] = sweep_leg(torch, H, dev, tuned, slots=args.slots,
                                         n_find=N_FIND if args.slots == SLOTS else args.slots)
