@@ -136,35 +136,15 @@ __device__ __forceinline__ bool claim_store(const View& v, uint32_t b, uint32_t 
   return false;
 }
 
-// Claim for the eviction phase: publish with CAS(EMPTY -> word).  An evictor
-// holding the bucket lock may exchange a claimed-but-unpublished slot (it then
-// reads EMPTY as its victim and stops); the CAS then fails and this claim
-// looks for another bit.  Bits only get cleared in this phase, so the loop
-// ends after at most S successful fetch_ands.
-template <int S>
-__device__ __forceinline__ bool claim_cas(const View& v, uint32_t b, uint64_t word,
-                                          uint32_t hint = 0) {
-  // `hint`: a free mask of bucket b read moments ago, used as the first guess
-  // (the fetch_and result is the authority either way)
-  uint32_t fm = hint ? hint : ld_relaxed32(v.masks + b);
-  for (int t = 0; t <= 2 * S && fm; ++t) {
-    const uint32_t s = __ffs(fm) - 1;
-    const uint32_t bit = 1u << s;
-    const uint32_t old = atomicAnd(v.masks + b, ~bit);
-    if (old & bit) {
-      unsigned long long* sp = ull(v.buckets + static_cast<uint64_t>(b) * S + s);
-      if (atomicCAS(sp, kEmptyWord, word) == kEmptyWord) return true;
-      fm = ld_relaxed32(v.masks + b);
-    } else {
-      fm = old;
-    }
-  }
-  return false;
-}
-// The claim of the phased eviction kernel: fetch_and on the free mask, then a
-// plain store.  No CAS is needed there: in that phase slots only go from
-// EMPTY to occupied (there are no erases), and a chain exchanges only a
-// slot it saw occupied, so nothing else writes a claimed, unpublished slot.
+// The claim of the eviction kernel and of the single-kernel batch: fetch_and
+// on the free mask, then a plain store.  The bit makes the slot the
+// claimer's, and nothing else writes a slot while it is EMPTY: in the
+// eviction phase slots only go from EMPTY to occupied (there are no erases)
+// and a chain exchanges only a slot it saw occupied; in the single-kernel
+// batch every other write to a bucket word is a CAS whose expected word is
+// not EMPTY (an erase's, a replace's, a chain's swap).  `hint`: a free mask
+// of bucket b read moments ago, used as the first guess (the fetch_and result
+// is the authority either way).
 template <int S>
 __device__ __forceinline__ bool claim_pub(const View& v, uint32_t b, uint64_t word,
                                           uint32_t hint = 0) {
@@ -1632,111 +1612,122 @@ __global__ void __launch_bounds__(kOvfThreads, HIVE_OVF_MIN_BLOCKS)
 // Here finds, erases, replaces, claims and eviction chains of one batch run
 // at the same time, so a lookup can race with a chain that has taken a word
 // out of a bucket and not yet put it down.  Each bucket has a version word:
-// bits 16..31 count the chains holding a word that was taken out of this
-// bucket (in transit), bits 0..15 count chain steps that finished.  A chain
-// raises the transit count of a bucket before it swaps a word out of it and
-// lowers it (bumping the step count) once that word sits in its other bucket
-// or in the stash, with a fence on each side.  A lookup reads the versions of
-// both candidate buckets before probing and again after a miss; the miss
-// stands only if neither bucket had a word in transit and neither version
-// moved, otherwise the op probes again.  A hit needs no check: the word was
-// observed in place.  Because erases now run beside chains, a chain swaps its
-// victim with a CAS on the word it read (never onto an EMPTY slot), and every
-// claim publishes with a CAS, exactly as in the eviction kernel.
+// bits 16..31 count the chains holding, in transit, a word whose BitHash1
+// bucket this is, bits 0..15 count chain steps that finished.  A chain
+// raises the transit count of the BitHash1 bucket of the word it is about to
+// swap out (whichever of its two buckets that word sits in) and lowers it
+// (bumping the step count) once that word sits in its other bucket or in the
+// stash, with a fence on each side.  A lookup of key k reads the version of
+// k's BitHash1 bucket before probing and again after a miss: one word covers
+// every move of k.  The miss stands only if no word was in transit there and
+// the version did not move; otherwise the op probes again.  A hit needs no
+// check: the word was observed in place.  Because erases now run beside
+// chains, a chain swaps its victim with a CAS on the word it read (never
+// onto an EMPTY slot); claims then own their slot by its free bit alone.
 constexpr uint32_t kTransit = 1u << 16;
 constexpr uint32_t kFusedRetryLimit = 1u << 14;
 
 __device__ __forceinline__ void transit_begin(const View& v, uint32_t b) {
   atomicAdd(v.vers + b, kTransit);
-  __threadfence();
+  fence_acq_rel_gpu();
 }
 __device__ __forceinline__ void transit_end(const View& v, uint32_t b) {
-  __threadfence();
+  fence_acq_rel_gpu();
   atomicAdd(v.vers + b, 1u - kTransit);
 }
 
-// Steps 3-4 for one new key whose candidate buckets had no free slot, run by
-// the warp inside the single-kernel batch.  Returns 1 placed, 2 stashed,
-// 3 no room (pending or FULL, decided by the caller).
+// Steps 3-4 for one new key whose candidate buckets had no free slot, inside
+// the single-kernel batch.  One chain per lane: the lanes of a warp carry up
+// to 32 chains at once, each on its own (they may diverge; a chain holds at
+// most one bucket lock at a time and waits for it a bounded number of
+// tries).  A chain is a run of dependent round trips, so carrying many at
+// once is what keeps the step short; a warp-wide chain left 31 lanes idle
+// per round trip.  The caller has already tried both free masks and holds a
+// stash reservation in `oc`.  Each round reads the bucket in hand 8 words at
+// a time with the free masks of those words' other buckets, and stops at the
+// first word that could move on at once (the victim); if none could, the
+// victim is the first occupied slot from a rotating start.  Under the bucket
+// lock the chain claims a free slot of the bucket for its word, or swaps the
+// victim out with a CAS on the exact word it re-read (never onto an EMPTY
+// slot), marking the version of the victim's BitHash1 bucket as holding a
+// word in transit until that word is down again.  Returns 1 placed, 2
+// stashed.
 template <int S>
-__device__ int fused_evict(const View& v, uint64_t word0, uint32_t b1, uint32_t b2,
-                           OvfCounters& oc, int lane) {
-  int outcome = 0;
-  if (lane == 0) {
-    const uint32_t m1 = ld_relaxed32(v.masks + b1);
-    const uint32_t m2 = ld_relaxed32(v.masks + b2);
-    if ((m1 && claim_cas<S>(v, b1, word0)) || (b2 != b1 && m2 && claim_cas<S>(v, b2, word0))) {
-      outcome = 1;
-      ++oc.claim;
-    } else {
-      if (oc.reserved_in != v.ctrl) {
-        if (oc.reserved_in) atomicSub(&oc.reserved_in->stash_claims, 1u);
-        oc.reserved_in = stash_reserve(v) ? v.ctrl : nullptr;
-      }
-      if (!oc.reserved_in) outcome = 3;
-    }
-  }
-  outcome = __shfl_sync(kFull, outcome, 0);
-  if (outcome != 0) return outcome;
-
+__device__ int chain_lane(const View& v, uint64_t word0, uint32_t b1, OvfCounters& oc) {
   uint64_t cur = word0;
   uint32_t b = b1;
-  uint32_t held = kNoOp;  // bucket the word in hand was taken out of
+  uint32_t held = kNoOp;  // version bucket marked for the word in hand
   bool placed = false;
   for (uint32_t r = 0; r < v.max_evictions; ++r) {
-    const uint64_t w =
-        lane < S ? ld_relaxed64(v.buckets + static_cast<uint64_t>(b) * S + lane) : kEmptyWord;
-    uint32_t am = 0;
-    if (w != kEmptyWord) {
-      const uint32_t k = key_of(w);
-      const uint32_t a1 = lh_bucket(bithash1(k), v.M, v.p);
-      const uint32_t a2 = lh_bucket(bithash2(k), v.M, v.p);
-      const uint32_t alt = (a1 == b) ? a2 : a1;
-      if (alt != b) am = ld_relaxed32(v.masks + alt);
+    uint64_t* B = v.buckets + static_cast<uint64_t>(b) * S;
+    unsigned occ = 0;
+    int vs = -1;
+    uint32_t vmask = 0;
+#pragma unroll 1
+    for (int f0 = 0; f0 < S; f0 += 8) {
+      uint64_t w[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ld_frag(B + f0 + 2 * q, w[2 * q], w[2 * q + 1]);
+      uint32_t am[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        am[k] = 0;
+        if (w[k] != kEmptyWord) {
+          occ |= 1u << (f0 + k);
+          const uint32_t kk = key_of(w[k]);
+          const uint32_t a1 = lh_bucket(bithash1(kk), v.M, v.p);
+          const uint32_t a2 = lh_bucket(bithash2(kk), v.M, v.p);
+          const uint32_t alt = (a1 == b) ? a2 : a1;
+          if (alt != b) am[k] = ld_relaxed32(v.masks + alt);
+        }
+      }
+#pragma unroll
+      for (int k = 7; k >= 0; --k)
+        if (am[k]) {
+          vs = f0 + k;
+          vmask = am[k];
+        }
+      if (vs >= 0) break;
     }
-    const unsigned gm = __ballot_sync(kFull, am != 0u);
-    const unsigned occ = __ballot_sync(kFull, lane < S && w != kEmptyWord);
-    const bool has_empty = __ballot_sync(kFull, lane < S && w == kEmptyWord) != 0u;
-    // victim: an occupied slot whose word can move on at once, else an
-    // occupied slot picked by rotation
-    uint32_t vs = S;
-    if (gm) {
-      vs = __ffs(gm) - 1;
-    } else if (occ) {
+    if (vs < 0 && occ) {
       const uint32_t start = (bithash2(key_of(cur)) + r) & (S - 1);
       const unsigned rot = (occ >> start) | (start ? (occ << (32 - start)) : 0u);
-      vs = (start + __ffs(rot) - 1) & 31;
+      vs = static_cast<int>((start + __ffs(rot) - 1) & (S - 1));
     }
-    const uint64_t wv = __shfl_sync(kFull, w, vs & 31);
-    const uint32_t vmask = __shfl_sync(kFull, am, vs & 31);
-    int res = 0;  // 0: swapped, 1: placed, 2: lock wait gave up, 3: redo the round
-    if (lane == 0) {
-      ++oc.rounds;
-      if (!lock_bucket(v, b)) {
-        res = 2;
-        ++oc.to;
+    int res;  // 0: swapped, 1: placed, 2: lock wait gave up, 3: redo the round
+    uint64_t wv = kEmptyWord;
+    uint32_t vb = 0;  // BitHash1 bucket of the victim: its version carries the transit mark
+    ++oc.rounds;
+    if (!lock_bucket(v, b)) {
+      res = 2;
+      ++oc.to;
+    } else {
+      ++oc.locks;
+      const uint32_t mb = ld_relaxed32(v.masks + b);
+      if (mb && claim_pub<S>(v, b, cur, mb)) {
+        res = 1;
+      } else if (vs < 0) {
+        res = 3;
       } else {
-        ++oc.locks;
-        if (has_empty && claim_cas<S>(v, b, cur)) {
-          res = 1;
-        } else if (vs >= S) {
-          res = 3;
+        uint64_t* sp = B + vs;
+        wv = ld_relaxed64(sp);
+        if (wv == kEmptyWord) {
+          res = 3;  // claimed and not yet published, or erased: look again
         } else {
-          transit_begin(v, b);
-          uint64_t* sp = v.buckets + static_cast<uint64_t>(b) * S + vs;
+          vb = lh_bucket(bithash1(key_of(wv)), v.M, v.p);
+          transit_begin(v, vb);
           if (atomicCAS(ull(sp), wv, cur) == wv) {
             res = 0;
           } else {
-            transit_end(v, b);
+            transit_end(v, vb);
             res = 3;
           }
         }
-        unlock_bucket(v, b);
       }
-      // the word in hand now sits in b (placed or swapped in)
-      if ((res == 0 || res == 1) && held != kNoOp) transit_end(v, held);
+      unlock_bucket(v, b);
     }
-    res = __shfl_sync(kFull, res, 0);
+    // the word in hand now sits in b (placed or swapped in)
+    if ((res == 0 || res == 1) && held != kNoOp) transit_end(v, held);
     if (res == 1) {
       placed = true;
       held = kNoOp;
@@ -1744,7 +1735,7 @@ __device__ int fused_evict(const View& v, uint64_t word0, uint32_t b1, uint32_t 
     }
     if (res == 2) break;
     if (res == 3) continue;
-    held = b;
+    held = vb;
     cur = wv;
     const uint32_t kc = key_of(cur);
     const uint32_t a1 = lh_bucket(bithash1(kc), v.M, v.p);
@@ -1752,31 +1743,141 @@ __device__ int fused_evict(const View& v, uint64_t word0, uint32_t b1, uint32_t 
     const uint32_t nb = (a1 == b) ? a2 : a1;
     if (nb == b) break;
     b = nb;
-    int ok = 0;
-    if (lane == 0) {
-      ok = claim_cas<S>(v, b, cur, vmask);
-      if (ok) transit_end(v, held);
-    }
-    if (__shfl_sync(kFull, ok, 0)) {
-      placed = true;
+    if (claim_pub<S>(v, b, cur, vmask)) {
+      transit_end(v, held);
       held = kNoOp;
+      placed = true;
       break;
     }
   }
-  if (lane == 0) {
-    if (placed && oc.reserved_in && ld_relaxed32(&v.ctrl->stash_claims) >= v.stash_cap) {
-      atomicSub(&v.ctrl->stash_claims, 1u);
-      oc.reserved_in = nullptr;
-    }
-    if (!placed) {
-      oc.reserved_in = nullptr;
-      const unsigned pos = atomicAdd(&v.ctrl->stash_tail, 1u);
-      st_relaxed64(v.stash_kv + pos, cur);
-      ++oc.stash;
-      if (held != kNoOp) transit_end(v, held);
-    }
+  if (placed && oc.reserved_in && ld_relaxed32(&v.ctrl->stash_claims) >= v.stash_cap) {
+    // every free stash word is reserved: give this one back
+    atomicSub(&v.ctrl->stash_claims, 1u);
+    oc.reserved_in = nullptr;
+  }
+  if (!placed) {
+    oc.reserved_in = nullptr;  // this append uses the reservation
+    const unsigned pos = atomicAdd(&v.ctrl->stash_tail, 1u);
+    st_relaxed64(v.stash_kv + pos, cur);
+    ++oc.stash;
+    if (held != kNoOp) transit_end(v, held);
   }
   return placed ? 1 : 2;
+}
+
+// A warp's queue of new keys whose two buckets were full, in shared memory:
+// kFusedQ packed words, then kFusedQ op indices.  The warp runs their chains
+// 32 at a time (one per lane) once 32 are waiting, and the rest before it
+// exits.  `n` is warp-uniform.
+constexpr uint32_t kFusedQ = 64;
+struct EvictQ {
+  uint64_t* words;
+  uint32_t* idx;
+  uint32_t n;
+};
+
+// Runs the chains of the first min(n, 32) queued keys, one per lane, and
+// moves the rest to the front (warp-wide).  Each key first tries both free
+// masks again (slots may have been freed since); the keys still without room
+// take a stash reservation for the warp's chains with one atomic, then run
+// their chains.
+template <int S>
+__device__ void fused_drain(const View& v, EvictQ& q, uint8_t* status, const List& pend,
+                            int resizable, OvfCounters& oc, int lane) {
+  __syncwarp();
+  const uint32_t m = q.n < 32 ? q.n : 32u;
+  const bool has = static_cast<uint32_t>(lane) < m;
+  const uint64_t word = has ? q.words[lane] : kEmptyWord;
+  const uint32_t idx = has ? q.idx[lane] : kNoOp;
+  const uint32_t key = key_of(word);
+  const uint32_t b1 = lh_bucket(bithash1(key), v.M, v.p);
+  const uint32_t b2 = lh_bucket(bithash2(key), v.M, v.p);
+  int out = 0;  // 1 placed, 2 stashed, 3 no room
+  if (has) {
+    const uint32_t m1 = ld_relaxed32(v.masks + b1);
+    const uint32_t m2 = ld_relaxed32(v.masks + b2);
+    if ((m1 && claim_pub<S>(v, b1, word, m1)) ||
+        (b2 != b1 && m2 && claim_pub<S>(v, b2, word, m2))) {
+      out = 1;
+      ++oc.claim;
+    }
+  }
+  // a chain may end in the stash, so it holds a reservation (kept by the lane
+  // for its later chains unless a stash append uses it)
+  const bool need_res = has && out == 0 && oc.reserved_in != v.ctrl;
+  const unsigned rm = __ballot_sync(kFull, need_res);
+  if (rm) {
+    const int leader = __ffs(rm) - 1;
+    const unsigned k = __popc(rm);
+    unsigned c0 = 0;
+    if (lane == leader) c0 = atomicAdd(&v.ctrl->stash_claims, k);
+    c0 = __shfl_sync(kFull, c0, leader);
+    const unsigned ok_n = c0 >= v.stash_cap ? 0u : min(k, v.stash_cap - c0);
+    if (lane == leader && ok_n < k) atomicSub(&v.ctrl->stash_claims, k - ok_n);
+    if (need_res) {
+      const unsigned rank = __popc(rm & ((1u << lane) - 1u));
+      oc.reserved_in = (rank < ok_n || stash_reserve(v)) ? v.ctrl : nullptr;
+    }
+  }
+  if (has && out == 0) out = oc.reserved_in == v.ctrl ? chain_lane<S>(v, word, b1, oc) : 3;
+  __syncwarp();
+  if (has) {
+    if (out == 3) {
+      ++oc.pend;
+      if (resizable) {
+        // placed by the eviction kernel after the table grows; it writes the status
+        const unsigned p = atomicAdd(pend.count, 1u);
+        pend.words[p] = word;
+        pend.idx[p] = idx;
+      } else {
+        atomicOr(&v.ctrl->err, kErrFull);
+        if (status && idx != kNoOp) status[idx] = ST_FULL;
+      }
+    } else {
+      ++oc.added;
+      if (status && idx != kNoOp) status[idx] = ST_INSERTED;
+    }
+  }
+  // the keys after the first 32 move to the front
+  const uint32_t rest = q.n - m;
+  __syncwarp();
+  uint64_t mw = 0;
+  uint32_t mi = 0;
+  if (static_cast<uint32_t>(lane) < rest) {
+    mw = q.words[32 + lane];
+    mi = q.idx[32 + lane];
+  }
+  __syncwarp();
+  if (static_cast<uint32_t>(lane) < rest) {
+    q.words[lane] = mw;
+    q.idx[lane] = mi;
+  }
+  __syncwarp();
+  q.n = rest;
+}
+
+// One single-bucket probe round of the single-kernel batch: bucket `myb` of
+// every op in `need` copied into the warp's staging buffer (buffer bucket j
+// for op j) with 16-byte cp.async through L2 only, then waited for.  Each
+// copy starts after the version read (an acquire) that precedes it in
+// program order, and the wait ends before the fence ahead of the second
+// version read.
+template <int S>
+__device__ __forceinline__ void fused_stage(const View& v, uint64_t* sbuf, unsigned need,
+                                            uint32_t myb, int lane) {
+  constexpr int L = Geo<S>::L, Q = Geo<S>::Q;
+  const int q = lane / L, ql = lane % L;
+  __syncwarp();  // earlier reads of the buffer by any lane come first
+#pragma unroll 4
+  for (int r = 0; r < 32 / Q; ++r) {
+    const int bi = Q * r + q;
+    const uint32_t y = __shfl_sync(kFull, myb, bi);
+    if ((need >> bi) & 1u)
+      cp_async16_cg(sbuf + bi * S + 2 * ql, v.buckets + static_cast<uint64_t>(y) * S + 2 * ql);
+  }
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncwarp();
 }
 
 // Looks the op keys of the `need` lanes up in the stash words appended during
@@ -1802,76 +1903,124 @@ __device__ __forceinline__ bool stash_tail_find(const View& v, uint32_t from, ui
   return hit;
 }
 
-// Ops [32c, 32c + 32) of a mixed batch in the single-kernel mode.
+// A warp's queue of ops that take the checked probe, in shared memory:
+// kFusedQ words (value << 32 | key), then kFusedQ words (op << 32 | op index).
+// `n` is warp-uniform.
+struct OpQ {
+  uint64_t* kv;
+  uint64_t* oi;
+  uint32_t n;
+};
+
+// The checked probe of the first min(n, 32) queued ops, one per lane
+// (warp-wide); the rest move to the front.  Each attempt reads the version of
+// the BitHash1 bucket of every op still open, probes that bucket and, for the
+// ops still open, the BitHash2 bucket (each round staged in shared memory),
+// then the stash.  A hit is acted on at once: a find takes the staged value
+// (the word was seen in place), an erase or replace CASes the word it saw and
+// probes again if the CAS fails (the word moved).  A miss stands only if no
+// word of that version was in transit and the version did not move;
+// otherwise the op probes again.  New keys then claim a slot by its free bit;
+// keys whose two buckets are full join the warp's eviction queue.
 template <int S>
-__device__ __forceinline__ void run_chunk_fused(const View& v, uint32_t stash_n, const OpPtrs a,
-                                                uint32_t c, uint64_t n, const List pend,
-                                                int resizable, LaneCounters& cnt,
-                                                OvfCounters& oc, unsigned& retries, int lane) {
-  const uint32_t i = (c << 5) + lane;
-  const bool valid = i < n;
-  uint32_t op = valid ? static_cast<uint32_t>(__ldcs(a.ops + i)) : OP_FIND;
-  if (op > OP_ERASE) op = OP_FIND;
-  const uint32_t key = valid ? __ldcs(a.keys + i) : kEmptyKey;
-  uint32_t val = 0;
-  if (valid && op == OP_INSERT && a.vals) val = __ldcs(a.vals + i);
-  const bool reserved = valid && key >= kReservedKeyMin;
-  const bool live = valid && !reserved;
-  cnt.reserved |= reserved;
+__device__ void fused_checked(const View& v, uint32_t stash_n, const OpPtrs& a, OpQ& rq,
+                              EvictQ& q, const List& pend, int resizable, LaneCounters& cnt,
+                              OvfCounters& oc, unsigned& retries, int lane, uint64_t* sbuf) {
+  __syncwarp();
+  const uint32_t mq = rq.n < 32 ? rq.n : 32u;
+  const bool has = static_cast<uint32_t>(lane) < mq;
+  const uint64_t kv = has ? rq.kv[lane] : 0u;
+  const uint64_t oi = has ? rq.oi[lane] : 0u;
+  {
+    const uint32_t rest = rq.n - mq;
+    uint64_t t0 = 0, t1 = 0;
+    if (static_cast<uint32_t>(lane) < rest) {
+      t0 = rq.kv[32 + lane];
+      t1 = rq.oi[32 + lane];
+    }
+    __syncwarp();
+    if (static_cast<uint32_t>(lane) < rest) {
+      rq.kv[lane] = t0;
+      rq.oi[lane] = t1;
+    }
+    __syncwarp();
+    rq.n = rest;
+  }
+  const uint32_t op = has ? static_cast<uint32_t>(oi >> 32) : OP_FIND;
+  const uint32_t key = has ? key_of(kv) : kEmptyKey;
+  const uint32_t val = val_of(kv);
+  const uint32_t i = static_cast<uint32_t>(oi);
   const uint32_t b1 = lh_bucket(bithash1(key), v.M, v.p);
   const uint32_t b2 = lh_bucket(bithash2(key), v.M, v.p);
-  bool done = !live;
-  uint8_t st = reserved ? ST_RESERVED : ST_NOT_FOUND;
+  bool done = !has;
+  uint8_t st = ST_NOT_FOUND;
   uint32_t outv = 0;
   uint32_t f1 = 0, s1 = S, f2 = 0, s2 = S;
   bool absent = false;  // a miss that survived the version check
-  // The first probe of a find or erase is optimistic: it reads no versions,
-  // since a hit needs no check (the word was seen in place).  A miss then
-  // probes again under the version check.  Inserts, which mostly miss (new
-  // keys), take the checked probe from the start.
-  bool checked = op == OP_INSERT;
   for (uint32_t attempt = 0;; ++attempt) {
     const bool active = !done && !absent;
-    unsigned need = __ballot_sync(kFull, active);
+    const unsigned need = __ballot_sync(kFull, active);
     if (!need) break;
     if (attempt >= kFusedRetryLimit) {  // never expected: chains end in bounded time
       if (lane == 0) atomicOr(&v.ctrl->err, kErrTimeout);
       break;
     }
-    const bool unchecked_miss = attempt == 1 && active && !checked;
     if (attempt) {
-      const unsigned rep = __ballot_sync(kFull, active && !unchecked_miss);
-      retries += (lane == 0) ? __popc(rep) : 0u;
-      if (rep) __nanosleep(64u << min(attempt, 6u));
-      checked = true;
+      retries += (lane == 0) ? __popc(need) : 0u;
+      __nanosleep(64u << min(attempt, 6u));
     }
-    uint32_t v1 = 0, v2 = 0;
-    if (active && checked) {
-      v1 = ld_acquire32(v.vers + b1);
-      v2 = ld_acquire32(v.vers + b2);
+    const uint32_t v1 = active ? ld_acquire32(v.vers + b1) : 0u;
+    // the stash words appended so far by this kernel (read with the probes: a
+    // word appended later was in transit from one of the op's buckets, which
+    // the second version read catches)
+    const uint32_t tail = ld_relaxed32(&v.ctrl->stash_tail);
+    PendCas pc{0, 0, 0, 0, 0};
+    // the BitHash1 bucket of every open op
+    uint32_t m = (active && op == OP_INSERT) ? ld_relaxed32(v.masks + b1) : 0u;
+    cnt.probes += __popc(need);
+    fused_stage<S>(v, sbuf, need, b1, lane);
+    if (active)
+      scan_staged_one<kModeMixed, S>(v, sbuf, lane, b1, key, val, op, m, done, st, outv, f1, s1,
+                                     pc);
+    // the BitHash2 bucket of the ops still open
+    const unsigned need2 = __ballot_sync(kFull, active && !done);
+    if (need2) {
+      m = (active && !done && op == OP_INSERT) ? ld_relaxed32(v.masks + b2) : 0u;
+      cnt.probes += __popc(need2);
+      fused_stage<S>(v, sbuf, need2, b2, lane);
+      if (active && !done)
+        scan_staged_one<kModeMixed, S>(v, sbuf, lane, b2, key, val, op, m, done, st, outv, f2,
+                                       s2, pc);
     }
+    // an erase or replace is done once its CAS has succeeded
     bool retry = false;
-    cnt.probes += __popc(need);
-    probe<kModeMixed, S, true>(v, need, b1, key, val, op, lane, done, st, outv, f1, s1, cnt,
-                               retry);
-    need = __ballot_sync(kFull, active && !done && !retry);
-    cnt.probes += __popc(need);
-    if (need)
-      probe<kModeMixed, S, true>(v, need, b2, key, val, op, lane, done, st, outv, f2, s2, cnt,
-                                 retry);
+    if (pc.kind) {
+      if (pc.old == pc.cur) {
+        if (pc.kind == 1) {
+          atomicOr(v.masks + pc.b, 1u << pc.slot);
+          cnt.size_delta -= 1;
+        } else {
+          cnt.replaced += 1;
+        }
+      } else {
+        done = false;
+        retry = true;
+        st = ST_NOT_FOUND;
+      }
+    }
     // the stash: the sorted prefix, then what this kernel appended
-    bool miss = active && !done && !retry;
+    const bool miss = active && !done && !retry;
     uint32_t pos = 0;
     bool shit = false;
     if (miss && stash_n) {
       cnt.stash_lookups += 1;
       shit = stash_find(v, stash_n, key, pos);
     }
-    const uint32_t tail = ld_relaxed32(&v.ctrl->stash_tail);
     const unsigned tneed = __ballot_sync(kFull, miss && !shit);
     if (tneed && tail > stash_n) {
       uint32_t tp = 0;
-      if (stash_tail_find(v, stash_n, min(tail, v.stash_cap), tneed, key, lane, tp) && miss && !shit) {
+      if (stash_tail_find(v, stash_n, min(tail, v.stash_cap), tneed, key, lane, tp) && miss &&
+          !shit) {
         shit = true;
         pos = tp;
       }
@@ -1904,16 +2053,15 @@ __device__ __forceinline__ void run_chunk_fused(const View& v, uint32_t stash_n,
         }
       }
     }
-    if (active && !done && !retry && checked) {
-      __threadfence();
-      const uint32_t w1 = ld_acquire32(v.vers + b1);
-      const uint32_t w2 = ld_acquire32(v.vers + b2);
-      absent = v1 < kTransit && v2 < kTransit && v1 == w1 && v2 == w2;
+    if (active && !done && !retry) {
+      fence_acq_rel_gpu();
+      const uint32_t w1 = ld_relaxed32(v.vers + b1);
+      absent = v1 < kTransit && v1 == w1;
     }
   }
 
   // New keys: claim in the preferred bucket (two-choice), else the other;
-  // keys that find both full run the eviction chain below.
+  // keys that find both full join the eviction queue.
   bool to_evict = false;
   if (absent && op == OP_INSERT) {
     const uint64_t word = pack(key, val);
@@ -1922,8 +2070,8 @@ __device__ __forceinline__ void run_chunk_fused(const View& v, uint32_t stash_n,
     const uint32_t ob = first1 ? b2 : b1, os = first1 ? s2 : s1;
     bool placed = false;
     if (f1 + f2 > 0) {
-      placed = claim_cas<S>(v, tb, word, ts < S ? (1u << ts) : 0u);
-      if (!placed && ob != tb) placed = claim_cas<S>(v, ob, word, os < S ? (1u << os) : 0u);
+      placed = claim_pub<S>(v, tb, word, ts < S ? (1u << ts) : 0u);
+      if (!placed && ob != tb) placed = claim_pub<S>(v, ob, word, os < S ? (1u << os) : 0u);
     }
     if (placed) {
       st = ST_INSERTED;
@@ -1934,44 +2082,117 @@ __device__ __forceinline__ void run_chunk_fused(const View& v, uint32_t stash_n,
       cnt.overflowed += 1;
     }
   }
-  for (unsigned m = __ballot_sync(kFull, to_evict); m; m &= m - 1) {
-    const int src = __ffs(m) - 1;
-    const uint64_t wj = __shfl_sync(kFull, pack(key, val), src);
-    const uint32_t x1 = __shfl_sync(kFull, b1, src);
-    const uint32_t x2 = __shfl_sync(kFull, b2, src);
-    const int out = fused_evict<S>(v, wj, x1, x2, oc, lane);
-    if (lane == 0) {  // the warp's eviction counters live in lane 0
-      if (out == 3)
-        ++oc.pend;
-      else
-        ++oc.added;
+  if (has) {
+    if (a.status && !to_evict) a.status[i] = st;
+    if (a.vals_out) a.vals_out[i] = outv;
+  }
+  const unsigned em = __ballot_sync(kFull, to_evict);
+  if (em) {
+    // q.n < 32 here, so the queue holds the new entries
+    if (to_evict) {
+      const uint32_t r = q.n + __popc(em & ((1u << lane) - 1u));
+      q.words[r] = pack(key, val);
+      q.idx[r] = i;
     }
-    if (lane == src) {
-      if (out == 3) {
-        if (resizable) {
-          const unsigned p = atomicAdd(pend.count, 1u);
-          pend.words[p] = wj;
-          pend.idx[p] = i;
-          st = 0xFF;  // written by the pending pass
-        } else {
-          atomicOr(&v.ctrl->err, kErrFull);
-          st = ST_FULL;
-        }
-      } else {
-        st = ST_INSERTED;
-      }
+    q.n += __popc(em);
+    if (q.n >= 32) fused_drain<S>(v, q, a.status, pend, resizable, oc, lane);
+  }
+}
+
+// Ops [32c, 32c + 32) of a mixed batch in the single-kernel mode (one op per
+// lane).  Finds and erases probe first without reading versions, since a hit
+// needs no check (the word was seen in place): the BitHash1 bucket of each,
+// then the BitHash2 bucket of those still open, staged in shared memory.
+// Their misses, and erases whose CAS failed (the word moved), join the warp's
+// queue for the checked probe; so do all inserts, which mostly miss (new
+// keys) and would have to probe again.  The checked probe runs 32 queued ops
+// at a time.
+template <int S>
+__device__ __forceinline__ void run_chunk_fused(const View& v, uint32_t stash_n, const OpPtrs a,
+                                                uint32_t c, uint64_t n, const OpIn& in,
+                                                const List pend, int resizable,
+                                                LaneCounters& cnt, OvfCounters& oc,
+                                                unsigned& retries, int lane, uint64_t* sbuf,
+                                                OpQ& rq, EvictQ& q) {
+  const uint32_t i = (c << 5) + lane;
+  const bool valid = i < n;
+  const uint32_t op = in.op, key = in.key, val = in.val;
+  const bool reserved = valid && key >= kReservedKeyMin;
+  const bool live = valid && !reserved;
+  cnt.reserved |= reserved;
+  const uint32_t b1 = lh_bucket(bithash1(key), v.M, v.p);
+  const uint32_t b2 = lh_bucket(bithash2(key), v.M, v.p);
+  const bool open = live && op != OP_INSERT;
+  bool done = false;
+  uint8_t st = reserved ? ST_RESERVED : ST_NOT_FOUND;
+  uint32_t outv = 0;
+  uint32_t fc = 0, fs = S;  // unused: finds and erases claim nothing
+  PendCas pc{0, 0, 0, 0, 0};
+  const unsigned need = __ballot_sync(kFull, open);
+  if (need) {
+    cnt.probes += __popc(need);
+    fused_stage<S>(v, sbuf, need, b1, lane);
+    if (open)
+      scan_staged_one<kModeMixed, S>(v, sbuf, lane, b1, key, val, op, 0u, done, st, outv, fc, fs,
+                                     pc);
+    const unsigned need2 = __ballot_sync(kFull, open && !done);
+    if (need2) {
+      cnt.probes += __popc(need2);
+      fused_stage<S>(v, sbuf, need2, b2, lane);
+      if (open && !done)
+        scan_staged_one<kModeMixed, S>(v, sbuf, lane, b2, key, val, op, 0u, done, st, outv, fc,
+                                       fs, pc);
     }
   }
-  if (valid) {
-    if (a.status && st != 0xFF) a.status[i] = st;
+  if (pc.kind) {
+    if (pc.old == pc.cur) {
+      atomicOr(v.masks + pc.b, 1u << pc.slot);  // erases only here
+      cnt.size_delta -= 1;
+    } else {
+      done = false;
+      st = ST_NOT_FOUND;
+    }
+  }
+  const bool to_check = live && !done;
+  if (valid && !to_check) {
+    if (a.status) a.status[i] = st;
     if (a.vals_out) __stcs(a.vals_out + i, outv);
   }
+  const unsigned cm = __ballot_sync(kFull, to_check);
+  if (cm) {
+    // rq.n < 32 here, so the queue holds the new entries
+    if (to_check) {
+      const uint32_t r = rq.n + __popc(cm & ((1u << lane) - 1u));
+      rq.kv[r] = pack(key, val);
+      rq.oi[r] = (static_cast<uint64_t>(op) << 32) | i;
+    }
+    rq.n += __popc(cm);
+    if (rq.n >= 32)
+      fused_checked<S>(v, stash_n, a, rq, q, pend, resizable, cnt, oc, retries, lane, sbuf);
+  }
+}
+
+// Shared-memory words per warp of the single-kernel batch: one staging round
+// (32 buckets), the checked-probe queue (2 kFusedQ words), then the eviction
+// queue (kFusedQ words and kFusedQ indices).
+__host__ __device__ constexpr int fused_warp_words(int S) {
+  return 32 * S + 3 * static_cast<int>(kFusedQ) + static_cast<int>(kFusedQ) / 2;
+}
+__host__ __device__ constexpr size_t fused_smem(int S) {
+  return static_cast<size_t>(kOpsThreads / 32) * 8u * fused_warp_words(S);
 }
 
 template <int S>
 __global__ void __launch_bounds__(kOpsThreads, 3)
     k_fused(View v, OpPtrs a, uint64_t n, List pend, int resizable) {
+  extern __shared__ __align__(16) uint64_t fused_smem_words[];
   const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  uint64_t* mine = fused_smem_words + static_cast<size_t>(wib) * fused_warp_words(S);
+  uint64_t* sbuf = mine;
+  OpQ rq{mine + 32 * S, mine + 32 * S + kFusedQ, 0};
+  EvictQ q{mine + 32 * S + 2 * kFusedQ, reinterpret_cast<uint32_t*>(mine + 32 * S + 3 * kFusedQ),
+           0};
   const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t nchunks = static_cast<uint32_t>((n + 31) >> 5);
@@ -1979,13 +2200,46 @@ __global__ void __launch_bounds__(kOpsThreads, 3)
   LaneCounters cnt;
   OvfCounters oc;
   unsigned retries = 0;
-  for (uint32_t c = warp0; c < nchunks; c += nwarps)
-    run_chunk_fused<S>(v, stash_n, a, c, n, pend, resizable, cnt, oc, retries, lane);
-  release_reservation(oc, lane == 0);
-  flush_ovf_counters(v, oc, lane == 0);
-  flush_counters(v, cnt, lane);
-  if (lane == 0 && retries)
-    atomicAdd(&v.ctrl->stats[kStFusedRetries], static_cast<unsigned long long>(retries));
+  // inputs are loaded one chunk ahead
+  OpIn nxt{};
+  if (warp0 < nchunks) nxt = load_in<kModeMixed>(a, warp0, n, lane);
+  for (uint32_t c = warp0; c < nchunks; c += nwarps) {
+    const OpIn cur = nxt;
+    if (c + nwarps < nchunks) nxt = load_in<kModeMixed>(a, c + nwarps, n, lane);
+    run_chunk_fused<S>(v, stash_n, a, c, n, cur, pend, resizable, cnt, oc, retries, lane, sbuf,
+                       rq, q);
+  }
+  while (rq.n) fused_checked<S>(v, stash_n, a, rq, q, pend, resizable, cnt, oc, retries, lane, sbuf);
+  while (q.n) fused_drain<S>(v, q, a.status, pend, resizable, oc, lane);
+  // counters: one atomic per counter and block
+  // (and the lanes' unused stash reservations go back in one atomic)
+  __shared__ unsigned sum[9];
+  if (threadIdx.x < 9) sum[threadIdx.x] = 0;
+  __syncthreads();
+  {
+    const unsigned c9[9] = {oc.claim, oc.rounds, oc.locks, oc.to, oc.stash, oc.pend, oc.added,
+                            retries, oc.reserved_in ? 1u : 0u};
+    oc.reserved_in = nullptr;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const unsigned t = __reduce_add_sync(kFull, c9[k]);
+      if (lane == 0 && t) atomicAdd(&sum[k], t);
+    }
+  }
+  flush_counters_block(v, cnt, lane, sbuf, fused_smem_words, fused_warp_words(S));
+  if (threadIdx.x == 0) {
+    OvfCounters b;
+    b.claim = sum[0];
+    b.rounds = sum[1];
+    b.locks = sum[2];
+    b.to = sum[3];
+    b.stash = sum[4];
+    b.pend = sum[5];
+    b.added = sum[6];
+    flush_ovf_counters(v, b, true);
+    if (sum[7]) atomicAdd(&v.ctrl->stats[kStFusedRetries], static_cast<unsigned long long>(sum[7]));
+    if (sum[8]) atomicSub(&v.ctrl->stash_claims, sum[8]);
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -2443,9 +2697,11 @@ cudaError_t launch_fused(const View& v, const uint8_t* ops, const uint32_t* keys
   if (blocks == 0) blocks = 1;
   const OpPtrs a{ops, keys, vals, vals_out, nullptr, status};
   if (v.S == 16)
-    k_fused<16><<<static_cast<unsigned>(blocks), kOpsThreads, 0, s>>>(v, a, n, pend, resizable);
+    k_fused<16><<<static_cast<unsigned>(blocks), kOpsThreads, fused_smem(16), s>>>(v, a, n, pend,
+                                                                                   resizable);
   else
-    k_fused<32><<<static_cast<unsigned>(blocks), kOpsThreads, 0, s>>>(v, a, n, pend, resizable);
+    k_fused<32><<<static_cast<unsigned>(blocks), kOpsThreads, fused_smem(32), s>>>(v, a, n, pend,
+                                                                                   resizable);
   return cudaGetLastError();
 }
 
@@ -2646,7 +2902,10 @@ cudaError_t occupancy_s(Launch* L) {
                   : L->ops_threads == 512 ? occupancy_ops<S, 512>(L)
                                           : occupancy_ops<S, 256>(L);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused<S>, kOpsThreads, 0);
+  e = cudaFuncSetAttribute(k_fused<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(fused_smem(S)));
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused<S>, kOpsThreads, fused_smem(S));
   if (e != cudaSuccess) return e;
   L->fused_blocks_per_sm = b > 0 ? b : 1;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_multi_ops<S>, kOpsThreads, 0);

@@ -2,37 +2,47 @@
 the single-kernel batch safe against eviction chains in flight (the design
 of k_fused; the CUDA kernel is covered by tests/test_gpu_fused.py).
 
-A chain moves key K out of one candidate bucket and into the other; a lookup
-of K probes both candidates.  Under sequential consistency (the fences of
+A chain moves key K out of one candidate bucket and into the other (or into
+the stash); a lookup of K probes both candidates and the stash.  The chain
+marks the version word of K's BitHash1 bucket (bucket 0 here) while K is in
+transit, whichever bucket K leaves, so the lookup reads that one version
+word before and after probing.  Under sequential consistency (the fences of
 the protocol order exactly these accesses), every interleaving of the
 chain's steps with the lookup's steps is enumerated, and a lookup that ends
-in a miss it accepts would be a lost key.  Without the version marks the same
-enumeration finds such interleavings, so the check is not vacuous."""
+in a miss it accepts would be a lost key.  Without the marks, or with marks
+on the bucket K leaves while the lookup reads only bucket 0's version, the
+same enumeration finds such interleavings, so the check is not vacuous."""
 import itertools
 
 T = 1 << 16  # transit unit of a version word
 
 
-def chain_steps(moves, marks=True):
-    """Steps of one chain that moves K along `moves` = [(src, dst), ...]."""
+STASH = 2  # the stash, as a third place K can be
+
+
+def chain_steps(moves, marks="key"):
+    """Steps of one chain that moves K along `moves` = [(src, dst), ...].
+    marks: "key" marks K's BitHash1 bucket (0), "src" the bucket K leaves,
+    None leaves the versions alone."""
     steps = []
     for src, dst in moves:
+        m = 0 if marks == "key" else src
         if marks:
-            steps.append(("mark", src))
+            steps.append(("mark", m))
         steps.append(("out", src))
         steps.append(("in", dst))
         if marks:
-            steps.append(("unmark", src))
+            steps.append(("unmark", m))
     return steps
 
 
-READER = [("v0",), ("probe", 0), ("probe", 1), ("v1",)]
+READER = [("v0",), ("probe", 0), ("probe", 1), ("probe", STASH), ("v1",)]
 
 
 def run(order, writer, start):
     """Execute one interleaving; returns the lookup's verdict."""
     where = {start}
-    ver = [0, 0]
+    ver = [0, 0, 0]
     wi = ri = 0
     found = False
     v_before = v_after = None
@@ -52,14 +62,14 @@ def run(order, writer, start):
             step = READER[ri]
             ri += 1
             if step[0] == "v0":
-                v_before = tuple(ver)
+                v_before = ver[0]
             elif step[0] == "probe":
                 found |= step[1] in where
             else:
-                v_after = tuple(ver)
+                v_after = ver[0]
     if found:
         return "hit"
-    quiet = all(v < T for v in v_before) and v_before == v_after
+    quiet = v_before < T and v_before == v_after
     return "miss" if quiet else "retry"
 
 
@@ -84,18 +94,37 @@ def test_two_moves_never_lose_the_key():
     assert "miss" not in verdicts(chain_steps([(0, 1), (1, 0)]), start=0)
 
 
-def test_reverse_probe_order_is_also_safe():
+def test_moves_from_the_other_bucket_never_lose_the_key():
+    # K starts in its BitHash2 bucket and moves 1 -> 0 -> 1
+    assert "miss" not in verdicts(chain_steps([(1, 0), (0, 1)]), start=1)
+
+
+def test_a_move_into_the_stash_never_loses_the_key():
+    # a chain that gives up puts the word it holds in the stash
+    assert "miss" not in verdicts(chain_steps([(0, 1), (1, STASH)]), start=0)
+    assert "miss" not in verdicts(chain_steps([(1, STASH)]), start=1)
+
+
+def test_every_probe_order_is_also_safe():
     global READER
     saved = READER
     try:
-        READER = [("v0",), ("probe", 1), ("probe", 0), ("v1",)]
-        assert "miss" not in verdicts(chain_steps([(0, 1), (1, 0)]), start=0)
+        for probes in itertools.permutations([0, 1, STASH]):
+            READER = [("v0",)] + [("probe", b) for b in probes] + [("v1",)]
+            for start, moves in ((0, [(0, 1), (1, 0)]), (1, [(1, 0), (0, STASH)])):
+                assert "miss" not in verdicts(chain_steps(moves), start=start), probes
     finally:
         READER = saved
 
 
 def test_without_marks_a_key_can_be_lost():
-    assert "miss" in verdicts(chain_steps([(0, 1)], marks=False), start=0)
+    assert "miss" in verdicts(chain_steps([(0, 1)], marks=None), start=0)
+
+
+def test_marks_on_the_left_bucket_miss_with_one_version_read():
+    # marking the bucket K leaves is not enough when the lookup reads only
+    # bucket 0's version: a move out of bucket 1 goes unseen
+    assert "miss" in verdicts(chain_steps([(1, 0), (0, 1)], marks="src"), start=1)
 
 
 def test_a_quiet_table_gives_hits():
