@@ -124,10 +124,13 @@ def _time_resizable(torch, H, W, slots, load_pct, mix, cfg, device, reps):
 
 
 def tune(slots: int, load_pct: float = 95, mix=(2, 1, 1), resizable: bool = False,
-         cache_path: str | None = None, reps: int = 2, space: dict | None = None,
+         cache_path: str | None = None, reps: int = 3, space: dict | None = None,
          device="cuda", force: bool = False) -> dict:
     """Best configuration (HiveTable keyword arguments) for the workload class;
-    `mix` is insert:find:erase.  Results are cached under workload_key()."""
+    `mix` is insert:find:erase.  Each candidate keeps its best of `reps` runs;
+    the runs go round the candidates in turn, so that a drift of the GPU or
+    host over the tuning time weighs on all of them alike.  Results are
+    cached under workload_key()."""
     import torch
 
     from . import hive as H
@@ -139,15 +142,21 @@ def tune(slots: int, load_pct: float = 95, mix=(2, 1, 1), resizable: bool = Fals
         return dict(cache[key]["config"])
     space = space or (RESIZE_SPACE if resizable else FIXED_SPACE)
     timer = _time_resizable if resizable else _time_fixed
-    results, ref = [], None
-    for cfg in candidates(space):
-        gops, out = timer(torch, H, W, slots, load_pct, mix, cfg, device, reps)
-        flat = [x for x in (out if resizable else [out]) for x in x]
-        if ref is None:
-            ref = flat
-        elif not all(torch.equal(a, b) for a, b in zip(ref, flat)):
-            raise RuntimeError(f"configuration {cfg} changed per-op results")
-        results.append({"config": cfg, "gops": gops})
+    cands = list(candidates(space))
+    best = [0.0] * len(cands)
+    ref = None
+    for rep in range(max(int(reps), 1)):
+        for j, cfg in enumerate(cands):
+            gops, out = timer(torch, H, W, slots, load_pct, mix, cfg, device, 1)
+            best[j] = max(best[j], gops)
+            if rep:
+                continue
+            flat = [x for x in (out if resizable else [out]) for x in x]
+            if ref is None:
+                ref = flat
+            elif not all(torch.equal(a, b) for a, b in zip(ref, flat)):
+                raise RuntimeError(f"configuration {cfg} changed per-op results")
+    results = [{"config": cfg, "gops": g} for cfg, g in zip(cands, best)]
     results.sort(key=lambda r: -r["gops"])
     cache[key] = {"config": results[0]["config"], "gops": results[0]["gops"],
                   "candidates": results, "device": torch.cuda.get_device_name(device)}
