@@ -345,8 +345,9 @@ def tables_leg(torch, H, dev, n_tables=1024, steps=8, seed=40):
     rng = np.random.default_rng(seed)
     caps = (np.exp(rng.uniform(10, 22, n_tables) * np.log(2)).astype(np.int64) // 32 + 1) * 32
     nops = np.exp(rng.uniform(6, 20, (steps, n_tables)) * np.log(2)).astype(np.int64)
-    # knobs from the autotuner for this class (resizable, 2^20 slots, 2:1:1)
-    tuned = AT.tune(1 << 20, 90, (2, 1, 1), True)
+    # knobs from the autotuner for this class: resizable tables of up to 2^22
+    # slots served in multi-table batches, 2:1:1
+    tuned = AT.tune(1 << 22, 90, (2, 1, 1), True, multi=True)
     K = int(tuned.get("resize_batch", 1024))
     knobs = {"max_evictions": int(tuned.get("max_evictions", 16)),
              "placement": int(tuned.get("placement", 0)),
@@ -906,7 +907,7 @@ def serving_leg(torch, H, dev, n_tables=64, n_requests=3000, seed=50, preload_lo
     pre = 1 << preload_log2
 
     from paper_2510_15095_gb300 import autotune as AT
-    tuned = AT.tune(1 << 20, 90, (2, 1, 1), True)  # the multi-table leg's class
+    tuned = AT.tune(1 << 22, 90, (2, 1, 1), True, multi=True)  # the multi-table leg's class
     knobs = {"bucket_slots": int(tuned.get("bucket_slots", 32)),
              "max_evictions": int(tuned.get("max_evictions", 16)),
              "placement": int(tuned.get("placement", 0))}

@@ -14,6 +14,11 @@ on the current GPU and caches the fastest in a JSON file.  The knobs:
 * resize_batch K (bucket pairs per split/merge launch, Section IV-C), for
   resizable tables: 256, 1024, 4096, 8192
 
+Tables served in multi-table batches (hive_multi_*) form classes of their
+own: a single resizable table reads its size back on every call, which costs
+more than the bucket width changes, so their candidates are timed on
+multi-table batches instead.
+
 Every candidate must return the same per-op results -- the knobs change
 layout and speed only -- and the tuner checks that as it goes.
 """
@@ -37,14 +42,15 @@ RESIZE_SPACE = {"bucket_slots": [16, 32], "resize_batch": [256, 1024, 4096, 8192
 LOAD_BANDS = (50, 80, 90, 95)
 
 
-def workload_key(slots: int, load_pct: float, mix, resizable: bool) -> str:
+def workload_key(slots: int, load_pct: float, mix, resizable: bool, multi: bool = False) -> str:
     """Class of a workload: log2 capacity band, nearest load band, op mix
-    normalised to tenths, fixed or resizable."""
+    normalised to tenths, fixed or resizable, single or multi-table."""
     cap = int(round(math.log2(max(int(slots), 32))))
     band = min(LOAD_BANDS, key=lambda b: abs(b - load_pct))
     tot = float(sum(mix))
     m = ":".join(str(int(round(10 * x / tot))) for x in mix)
-    return f"cap{cap}-load{band}-mix{m}-{'resizable' if resizable else 'fixed'}"
+    kind = "resizable" if resizable else "fixed"
+    return f"cap{cap}-load{band}-mix{m}-{kind}" + ("-multi" if multi else "")
 
 
 def load_cache(path: str | None = None) -> dict:
@@ -125,23 +131,24 @@ def _time_resizable(torch, H, W, slots, load_pct, mix, cfg, device, reps):
 
 def tune(slots: int, load_pct: float = 95, mix=(2, 1, 1), resizable: bool = False,
          cache_path: str | None = None, reps: int = 3, space: dict | None = None,
-         device="cuda", force: bool = False) -> dict:
+         device="cuda", force: bool = False, multi: bool = False) -> dict:
     """Best configuration (HiveTable keyword arguments) for the workload class;
     `mix` is insert:find:erase.  Each candidate keeps its best of `reps` runs;
     the runs go round the candidates in turn, so that a drift of the GPU or
     host over the tuning time weighs on all of them alike.  Results are
-    cached under workload_key()."""
+    cached under workload_key().  `multi`: the tables are served in
+    multi-table batches (capacities up to `slots`)."""
     import torch
 
     from . import hive as H
     from . import workload as W
 
-    key = workload_key(slots, load_pct, mix, resizable)
+    key = workload_key(slots, load_pct, mix, resizable, multi)
     cache = load_cache(cache_path)
     if key in cache and not force:
         return dict(cache[key]["config"])
     space = space or (RESIZE_SPACE if resizable else FIXED_SPACE)
-    timer = _time_resizable if resizable else _time_fixed
+    timer = _time_multi if multi else (_time_resizable if resizable else _time_fixed)
     cands = list(candidates(space))
     best = [0.0] * len(cands)
     ref = None
@@ -151,7 +158,7 @@ def tune(slots: int, load_pct: float = 95, mix=(2, 1, 1), resizable: bool = Fals
             best[j] = max(best[j], gops)
             if rep:
                 continue
-            flat = [x for x in (out if resizable else [out]) for x in x]
+            flat = [x for x in (out if (resizable or multi) else [out]) for x in x]
             if ref is None:
                 ref = flat
             elif not all(torch.equal(a, b) for a, b in zip(ref, flat)):
@@ -162,3 +169,64 @@ def tune(slots: int, load_pct: float = 95, mix=(2, 1, 1), resizable: bool = Fals
                   "candidates": results, "device": torch.cuda.get_device_name(device)}
     save_cache(cache, cache_path)
     return dict(results[0]["config"])
+
+
+def _time_multi(torch, H, W, slots, load_pct, mix, cfg, device, reps):
+    """64 tables of capacities log-uniform in [2^10, slots], half full, then
+    4 multi-table batches of log-uniform [2^6, 2^16] ops per table; resizable
+    tables when cfg names a resize_batch.  Times the batches (host clock
+    around the device work)."""
+    import random
+
+    rng = random.Random(4545)
+    n_tables, steps = 64, 4
+    hi = max(math.log2(max(int(slots), 1024)), 10.0)
+    caps = [(int(2 ** rng.uniform(10, hi)) // 32 + 1) * 32 for _ in range(n_tables)]
+    nops = [[int(2 ** rng.uniform(6, 16)) for _ in range(n_tables)] for _ in range(steps)]
+    tot = float(sum(mix))
+    ins_f, er_f = (int(10 * mix[0] / tot), 10), (int(10 * mix[2] / tot), 10)
+    knobs = {k: v for k, v in cfg.items() if k != "resize_batch"}
+    resizable = "resize_batch" in cfg
+    K = int(cfg.get("resize_batch", 1024))
+    # room for every insert of the run, so that no insert can find a table
+    # full (FULL outcomes would depend on the layout)
+    ins = [sum(nops[st][t] for st in range(steps)) * ins_f[0] // ins_f[1] for t in range(n_tables)]
+    room = [caps[t] + ins[t] * 10 // 9 + caps[t] // 2 + 64 * K for t in range(n_tables)]
+    best, out = float("inf"), None
+    for _ in range(reps):
+        tabs, counts = [], []
+        for t, cap in enumerate(caps):
+            if resizable:
+                tb = H.HiveTable(cap, max_slots=room[t], resizable=True, resize_batch=K, **knobs)
+            else:
+                tb = H.HiveTable(room[t], **knobs)
+            k, v = W.preload_t(torch, 9000 + t, cap // 2, device)
+            tb.insert(k, v, status=False)
+            tabs.append(tb)
+            counts.append(cap // 2)
+        work = []
+        for st in range(steps):
+            row = []
+            for t in range(n_tables):
+                ops, keys, vals, counts[t], n_ins = W.mixed_step_t(
+                    torch, 9000 + t, counts[t], nops[st][t], device, ins_f, er_f, salt=st)
+                row.append((ops, keys, vals, n_ins))
+            work.append(row)
+        res = [[(torch.empty(w[1].numel(), dtype=torch.int32, device=device),
+                 torch.empty(w[1].numel(), dtype=torch.uint8, device=device)) for w in row]
+               for row in work]
+        max_ops = max(sum(r) for r in nops) + 1
+        multi = H.HiveMulti(tabs, max_segments=n_tables, max_ops=max_ops, use_graph=False)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        for st in range(steps):
+            multi.execute([{"table": t, "ops": w[0], "keys": w[1], "vals": w[2],
+                            "n_insert": w[3], "vals_out": res[st][t][0],
+                            "status": res[st][t][1]} for t, w in enumerate(work[st])])
+        torch.cuda.synchronize(device)
+        best = min(best, time.perf_counter() - t0)
+        multi.close()
+        for tb in tabs:
+            tb.close()
+        out = [x for row in res for pair in row for x in pair]
+    return sum(sum(r) for r in nops) / best / 1e9, [out]

@@ -11,6 +11,7 @@ def test_workload_key_bands():
     assert A.workload_key(1 << 26, 95, (2, 1, 1), False) == "cap26-load95-mix5:2:2-fixed"
     assert A.workload_key((1 << 26) + 5, 94.2, (4, 4, 2), True) == "cap26-load95-mix4:4:2-resizable"
     assert A.workload_key(1000, 52, (1, 0, 0), False).startswith("cap10-load50-mix10:0:0")
+    assert A.workload_key(1 << 22, 90, (2, 1, 1), True, True) == "cap22-load90-mix5:2:2-resizable-multi"
 
 
 def test_candidates_cover_space():
@@ -46,3 +47,10 @@ def test_tune_on_gpu(tmp_path):
     rcfg = A.tune(1 << 18, 90, (4, 4, 2), True, cache_path=p,
                   space={"resize_batch": [256, 1024], "max_evictions": [16], "placement": [0]})
     assert rcfg["resize_batch"] in (256, 1024)
+    # tables served in multi-table batches: both widths, both resize batch
+    # sizes, identical per-op results (tune() checks it)
+    mcfg = A.tune(1 << 16, 90, (2, 1, 1), True, cache_path=p, multi=True, reps=1,
+                  space={"bucket_slots": [16, 32], "resize_batch": [256, 1024],
+                         "max_evictions": [16], "placement": [0]})
+    assert mcfg["bucket_slots"] in (16, 32)
+    assert any(k.endswith("-multi") for k in A.load_cache(p))
