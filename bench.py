@@ -969,6 +969,7 @@ def serving_leg(torch, H, dev, n_tables=64, n_requests=3000, seed=50, preload_lo
     sat_b = serve(reqs, False)
     check(reqs)
     end_live, end_slots = sizes["live"], sizes["slots"]
+    host_payload = host_payload_run(torch, SV, H, base, serve, ref)
     reqs = with_arrivals(zeros)
     sat_f = serve(reqs, True)
     check(reqs)
@@ -1000,7 +1001,41 @@ def serving_leg(torch, H, dev, n_tables=64, n_requests=3000, seed=50, preload_lo
                               "live_keys_max": int(max(end_live)),
                               "slots_max": int(max(end_slots)),
                               "committed_gb": float(sum(end_slots) * SV.SLOT_BYTES / 1e9)},
+            "host_payload": host_payload,
             "identical_results": bool(same[0]), "tuned": tuned}
+
+
+def host_payload_run(torch, SV, H, base, serve, ref):
+    """The serving leg's closed-loop batched run with every request's payload
+    (ops, keys, values in; values and statuses out) in pinned host memory,
+    which the multi-table kernels read and write in place across the CPU-GPU
+    link.  The arrays are views of one pinned buffer per field, filled before
+    the run; results must equal the device-payload run's."""
+    def pinned(ts, dtype, fill):
+        flat = torch.empty(sum(int(t.numel()) for t in ts), dtype=dtype, pin_memory=True)
+        out, off = [], 0
+        for t in ts:
+            n = int(t.numel())
+            v = flat[off:off + n]
+            if fill:
+                v.copy_(t)
+            out.append(v)
+            off += n
+        return out
+    ops = pinned([r.ops for r in base], torch.uint8, True)
+    keys = pinned([r.keys for r in base], torch.int32, True)
+    vals = pinned([r.vals for r in base], torch.int32, True)
+    vout = pinned([r.keys for r in base], torch.int32, False)
+    stat = pinned([r.ops for r in base], torch.uint8, False)
+    reqs = [SV.Request(r.rid, r.table, 0.0, o, k, v, r.n_insert, vo, st)
+            for r, o, k, v, vo, st in zip(base, ops, keys, vals, vout, stat)]
+    out = serve(reqs, False)
+    same = all(torch.equal(a.cpu(), r.status) and torch.equal(b.cpu(), r.vals_out)
+               for (a, b), r in zip(ref, reqs))
+    return {"batched_gops": out["gops"], "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"],
+            "identical_results": bool(same), "direct_access": H.host_direct_access(),
+            "h2d_bytes": int(sum(9 * int(r.keys.numel()) for r in base)),
+            "d2h_bytes": int(sum(5 * int(r.keys.numel()) for r in base))}
 
 
 # ---------------------------------------------------------------------------

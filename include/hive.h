@@ -350,6 +350,11 @@ typedef struct {
   uint32_t* vals_out;     /* [n] find results, 0 otherwise (device, nullable) */
   uint8_t* status;        /* [n] per-op status (device, nullable) */
 } hive_segment;
+/* "device" above: any address the kernels can use, which includes pinned or
+ * registered host memory (cudaMallocHost, cudaHostRegister): the kernels then
+ * read the inputs and write the results across the CPU-GPU link, at near
+ * device speed where hive_host_direct_access() reports 1.  The caller keeps
+ * such host arrays untouched until the batch has completed. */
 
 /* Flags of hive_multi_create. */
 enum {

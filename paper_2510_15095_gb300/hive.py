@@ -177,6 +177,19 @@ def _torch():
     return torch
 
 
+def _sptr(t, itemsize: int, n: int, name: str):
+    """Pointer of a segment array: a contiguous CUDA tensor, or a pinned CPU
+    tensor, which the kernels read and write in place through the
+    CPU-GPU link (at near device speed where host_direct_access() holds)."""
+    if t is not None and not t.is_cuda:
+        if not t.is_pinned():
+            raise ValueError(f"{name} must be a CUDA tensor or a pinned CPU tensor")
+        if not t.is_contiguous() or t.element_size() != itemsize or t.numel() < n:
+            raise ValueError(f"{name} must be contiguous with >= {n} {itemsize}-byte items")
+        return t.data_ptr()
+    return _dptr(t, itemsize, n, name)
+
+
 def _dptr(t, itemsize: int, n: int, name: str):
     """Device pointer of a contiguous CUDA tensor with >= n items of itemsize."""
     if t is None:
@@ -557,7 +570,8 @@ class HiveMulti:
 
     def execute(self, segments, stream=None):
         """segments: iterable of dicts with keys table, ops, keys and optionally
-        vals, vals_out, status (CUDA tensors) and n_insert (int)."""
+        vals, vals_out, status (CUDA tensors, or pinned CPU tensors that the
+        kernels use in place) and n_insert (int)."""
         segs = list(segments)
         arr = (Segment * max(len(segs), 1))()
         for i, g in enumerate(segs):
@@ -565,11 +579,11 @@ class HiveMulti:
             arr[i].table = int(g["table"])
             arr[i].n = n
             arr[i].n_insert = int(g.get("n_insert", n))
-            arr[i].ops = _dptr(g["ops"], 1, n, "ops")
-            arr[i].keys = _dptr(g["keys"], 4, n, "keys")
-            arr[i].vals = _dptr(g.get("vals"), 4, n, "vals")
-            arr[i].vals_out = _dptr(g.get("vals_out"), 4, n, "vals_out")
-            arr[i].status = _dptr(g.get("status"), 1, n, "status")
+            arr[i].ops = _sptr(g["ops"], 1, n, "ops")
+            arr[i].keys = _sptr(g["keys"], 4, n, "keys")
+            arr[i].vals = _sptr(g.get("vals"), 4, n, "vals")
+            arr[i].vals_out = _sptr(g.get("vals_out"), 4, n, "vals_out")
+            arr[i].status = _sptr(g.get("status"), 1, n, "status")
         _raise(self._L, self._L.hive_multi_execute(self._h, arr, len(segs), _stream_ptr(stream)))
 
     def bounds(self) -> list:

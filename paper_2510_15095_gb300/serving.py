@@ -1,7 +1,7 @@
 """Continuous-batching serving loop over many device-resident Hive tables.
 
-Requests (an op range on one table, device-resident payload) arrive over
-time.  The server keeps a FIFO of arrived requests and, whenever fewer than
+Requests (an op range on one table; payload in device memory, or in pinned
+host memory that the kernels read and write in place) arrive over time.  The server keeps a FIFO of arrived requests and, whenever fewer than
 `depth` batches are in flight, coalesces the oldest admissible requests into
 one multi-table batch (hive_multi_execute in asynchronous mode, replayed from
 a captured CUDA graph) and queues it on its stream.  A request is admissible
@@ -41,9 +41,9 @@ class Request:
     rid: int
     table: int
     arrival: float  # seconds after the run starts
-    ops: object  # CUDA uint8 tensor
-    keys: object  # CUDA int32 tensor
-    vals: object  # CUDA int32 tensor
+    ops: object  # uint8 tensor: CUDA, or pinned host memory used in place
+    keys: object  # int32 tensor, same memory as ops
+    vals: object  # int32 tensor, same memory as ops
     n_insert: int
     vals_out: object = None
     status: object = None
@@ -159,10 +159,15 @@ class HiveServer:
         request's done_at is filled in (seconds after start)."""
         torch = self.torch
         for r in reqs:
+            # results go where the payload is: device memory, or pinned host
+            # memory that the kernels write in place
+            pin = not r.keys.is_cuda
             if r.vals_out is None:
-                r.vals_out = torch.empty(r.n, dtype=torch.int32, device=r.keys.device)
+                r.vals_out = torch.empty(r.n, dtype=torch.int32, device=r.keys.device,
+                                         pin_memory=pin)
             if r.status is None:
-                r.status = torch.empty(r.n, dtype=torch.uint8, device=r.keys.device)
+                r.status = torch.empty(r.n, dtype=torch.uint8, device=r.keys.device,
+                                       pin_memory=pin)
         start = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         start.record(self.stream)

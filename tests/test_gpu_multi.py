@@ -38,7 +38,7 @@ def _batch(rng, live, ctr, seed, n_ins, n_er, n_fd):
     return ops[perm], keys[perm], vals[perm], ctr
 
 
-def _run(H, tables, dicts, policies, batches, use_graph, rng, seed0, skip_prob=0.2):
+def _run(H, tables, dicts, policies, batches, use_graph, rng, seed0, skip_prob=0.2, host=False):
     m = H.HiveMulti(tables, max_segments=2 * len(tables), max_ops=1 << 22, use_graph=use_graph)
     ctrs = [1_000_000 * (i + 1) for i in range(len(tables))]
     for b, (n_ins, n_er, n_fd) in enumerate(batches):
@@ -51,11 +51,18 @@ def _run(H, tables, dicts, policies, batches, use_graph, rng, seed0, skip_prob=0
             ni = int(rng.integers(0, n_ins + 1))
             ops, keys, vals, ctrs[t] = _batch(rng, live, ctrs[t], seed0 + t, ni,
                                              int(rng.integers(0, n_er + 1)), int(rng.integers(1, n_fd + 1)))
-            g = {"table": int(t), "ops": torch.from_numpy(ops).cuda(), "keys": H.to_device_u32(keys),
-                 "vals": H.to_device_u32(vals),
-                 "vals_out": torch.empty(keys.size, dtype=torch.int32, device="cuda"),
-                 "status": torch.empty(keys.size, dtype=torch.uint8, device="cuda"),
-                 "n_insert": int((ops == W.OP_INSERT).sum())}
+            if host:  # payload in pinned host memory, used in place by the kernels
+                g = {"table": int(t), "ops": torch.from_numpy(ops).pin_memory(),
+                     "keys": torch.from_numpy(keys.view(np.int32)).pin_memory(),
+                     "vals": torch.from_numpy(vals.view(np.int32)).pin_memory(),
+                     "vals_out": torch.empty(keys.size, dtype=torch.int32, pin_memory=True),
+                     "status": torch.empty(keys.size, dtype=torch.uint8, pin_memory=True)}
+            else:
+                g = {"table": int(t), "ops": torch.from_numpy(ops).cuda(),
+                     "keys": H.to_device_u32(keys), "vals": H.to_device_u32(vals),
+                     "vals_out": torch.empty(keys.size, dtype=torch.int32, device="cuda"),
+                     "status": torch.empty(keys.size, dtype=torch.uint8, device="cuda")}
+            g["n_insert"] = int((ops == W.OP_INSERT).sum())
             if policies[t] is not None:
                 policies[t].grow(len(dicts[t]), g["n_insert"])
             ev, est = dicts[t].execute(ops, keys, vals)
@@ -129,5 +136,24 @@ def test_multi_mixed_fixed_and_resizable_with_single_calls(H):
     pols[1].shrink(len(dicts[1]))
     assert tables[1].capacity() == S * pols[1].state[0]
     _run(H, tables, dicts, pols, [(800, 200, 500)] * 2, True, rng, 1400, skip_prob=0.0)
+    for tb in tables:
+        tb.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_multi_host_payload_segments(H, use_graph):
+    """Segments whose arrays are pinned host tensors: the kernels read the ops
+    and write the results in place across the CPU-GPU link; results, sizes,
+    capacities and contents equal the oracles', as with device arrays."""
+    rng = np.random.default_rng(31 if use_graph else 32)
+    n = 8
+    init = [1 << int(x) for x in rng.integers(10, 13, n)]
+    K = 32
+    tables = [H.HiveTable(sz, max_slots=1 << 20, resizable=True, resize_batch=K, bucket_slots=16)
+              for sz in init]
+    pols = [oracle.Policy(sz // 16, (1 << 20) // 16, K=K, S=16) for sz in init]
+    dicts = [oracle.Dict() for _ in tables]
+    _run(H, tables, dicts, pols, [(5_000, 500, 2_000)] * 3 + [(200, 6_000, 2_000)] * 2,
+         use_graph, rng, 1700, skip_prob=0.1, host=True)
     for tb in tables:
         tb.close()
