@@ -66,6 +66,8 @@ def parse_args():
                     help="fix the persisting L2 window of the free masks (-1: autotuned)")
     ap.add_argument("--block-threads", type=int, choices=[0, 128, 256, 512], default=0,
                     help="fix the bulk kernels' block shape (0: autotuned)")
+    ap.add_argument("--no-cpu-parallel", action="store_true",
+                    help="skip the parallel CPU baseline (whole step on all host cores)")
     ap.add_argument("--no-breakdown", action="store_true",
                     help="skip the insertion-step breakdown against load factor")
     ap.add_argument("--no-sweep", action="store_true",
@@ -252,6 +254,25 @@ def host_info() -> dict:
         except (OSError, subprocess.SubprocessError):
             pass
     return {"cpus": os.cpu_count(), "model": model or platform.machine()}
+
+
+def cpu_parallel_leg(w):
+    """A parallel CPU baseline, labelled apart from the oracle: the whole bench
+    step (every insert, find and mixed op of the workload) on all host cores,
+    the dictionary sharded by key over one std::unordered_map per thread
+    (oracle.sharded_step).  Its insert statuses and find flags are checked
+    against the workload's own expectations."""
+    import oracle
+    threads = os.cpu_count() or 1
+    sec, ist, fv, ff, mvo, mst = oracle.sharded_step(
+        threads, w["insert_keys"], w["insert_vals"], w["find_keys"], w["mix_ops"], w["mix_keys"],
+        w["mix_vals"])
+    ops = ist.size + ff.size + mst.size
+    ok = bool((ist == oracle.INSERTED).all() and np.array_equal(ff.astype(bool), w["is_hit"]))
+    return {"value": ops / sec / 1e9, "unit": "Gops/s", "threads": threads,
+            "kind": "sharded std::unordered_map (a CPU baseline, not the oracle)",
+            "sample": f"the whole step: {ist.size} inserts, {ff.size} finds, {mst.size} mixed ops",
+            "seconds": sec, "results_as_expected": ok, "host": host_info()}
 
 
 def oracle_sample(w, n_sample: int):
@@ -1329,6 +1350,8 @@ def main():
                "sample": f"{n} inserts + {n} finds + {n // 4} mixed ops (prefix of the workload), "
                          f"{dt:.1f} s single-threaded std::unordered_map",
                "host": host_info()}
+        if not args.no_cpu_parallel:
+            extra["cpu_parallel"] = cpu_parallel_leg(w)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gops/s", "n_gpus": world,

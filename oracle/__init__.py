@@ -36,7 +36,8 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", _SRC,
+                               "-o", tmp])
         os.replace(tmp, _SO)
     return _SO
 
@@ -64,6 +65,9 @@ def lib():
             L.orc_erase.argtypes = [vp, vp, u64, u8p]
             L.orc_execute.argtypes = [vp, vp, vp, vp, u64, vp, u8p]
             L.orc_dump.argtypes = [vp, vp, vp]
+            L.orc_sharded_step.argtypes = [C.c_int, vp, vp, u64, u8p, vp, u64, vp, u8p, vp, vp, vp,
+                                           u64, vp, u8p]
+            L.orc_sharded_step.restype = C.c_double
             L.orc_bithash1.argtypes = [u32]
             L.orc_bithash1.restype = u32
             L.orc_bithash2.argtypes = [u32]
@@ -186,6 +190,23 @@ def bithash_checksum(lo: int, hi: int) -> int:
     """Sum over keys lo..hi-1 of (BitHash1(k) + 2^32 BitHash2(k)) * (2k + 1)
     modulo 2^64 (see orc_bithash_checksum)."""
     return int(lib().orc_bithash_checksum(int(lo), int(hi)))
+
+
+def sharded_step(threads: int, ins_keys, ins_vals, find_keys, mix_ops, mix_keys, mix_vals):
+    """A parallel CPU baseline (orc_sharded_step): inserts, then finds, then a
+    mixed batch, on `threads` host threads over key-sharded maps.  Returns
+    (seconds, insert statuses, find values, find flags, mixed values, mixed
+    statuses); the results equal Dict's applied in the same order."""
+    ik, iv, fk = _u32(ins_keys), _u32(ins_vals), _u32(find_keys)
+    mo = np.ascontiguousarray(mix_ops, dtype=np.uint8)
+    mk, mv = _u32(mix_keys), _u32(mix_vals)
+    ist = np.empty(ik.size, np.uint8)
+    fv, ff = np.empty(fk.size, np.uint32), np.empty(fk.size, np.uint8)
+    mvo, mst = np.empty(mk.size, np.uint32), np.empty(mk.size, np.uint8)
+    sec = lib().orc_sharded_step(int(threads), _ptr(ik), _ptr(iv), ik.size, _ptr(ist), _ptr(fk),
+                                 fk.size, _ptr(fv), _ptr(ff), _ptr(mo), _ptr(mk), _ptr(mv),
+                                 mk.size, _ptr(mvo), _ptr(mst))
+    return float(sec), ist, fv, ff, mvo, mst
 
 
 def lh_address_many(h, M: int, p: int) -> np.ndarray:

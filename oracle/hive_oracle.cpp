@@ -27,6 +27,9 @@
 //  4. A checker of the table's structural invariants over a host copy of the
 //     device layout (Section III-A/B: packed words, freeMask, lock, stash).
 //
+//  5. A parallel CPU baseline for the benchmark (not part of the oracle's
+//     definition): the same dictionary sharded by key over host threads.
+//
 // Parity notes: items 1 and 3 are pinned by tests against a brute-force map,
 // closed forms and textbook linear-hashing properties; item 2 is pinned by
 // inverting each published mixing step and by Theorem 1's collision count;
@@ -34,8 +37,10 @@
 // is not unique under concurrency ("parity unpinned" for layout); only the
 // invariants apply to it.
 #include <algorithm>
+#include <chrono>
 #include <cstdint>
 #include <cstring>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -427,6 +432,57 @@ int orc_check_image(const uint64_t* buckets, const uint32_t* masks, const uint32
     if (nb != policy->nb_init && under_shrink(policy, live, nb)) return 7;
   }
   return 0;
+}
+
+// ---------------------------------------------------------------------------
+// 5. A parallel CPU baseline (not part of the oracle's definition): the bench
+//    step's three phases -- n_ins inserts, n_find finds, n_mix mixed ops --
+//    on T threads.  Each key belongs to one of T shards (the high bits of
+//    k * 0x9E3779B1, a multiplicative hash), and each shard is a
+//    std::unordered_map that one thread updates in array order.  Keys of
+//    different shards never interact, so every per-op result equals the
+//    single map's.  Per phase: the threads first sort the op indices of
+//    their slice of the array by shard (order kept), then each thread runs
+//    its shard's ops slice by slice.  Returns the seconds the three phases
+//    took, thread start-up included.
+// ---------------------------------------------------------------------------
+double orc_sharded_step(int T, const uint32_t* ik, const uint32_t* iv, uint64_t n_ins,
+                        uint8_t* ist, const uint32_t* fk, uint64_t n_find, uint32_t* fv,
+                        uint8_t* ff, const uint8_t* mo, const uint32_t* mk, const uint32_t* mv,
+                        uint64_t n_mix, uint32_t* mvo, uint8_t* mst) {
+  if (T < 1) T = 1;
+  std::vector<Dict> shard(T);
+  auto owner = [T](uint32_t k) {
+    return static_cast<int>((static_cast<uint64_t>(k * 0x9E3779B1u) * static_cast<uint64_t>(T)) >> 32);
+  };
+  // idx[slice][shard]: the slice's op indices of that shard, in order
+  std::vector<std::vector<std::vector<uint32_t>>> idx(T, std::vector<std::vector<uint32_t>>(T));
+  auto phase = [&](const uint32_t* keys, uint64_t n, auto&& apply) {
+    std::vector<std::thread> th;
+    for (int s = 0; s < T; ++s)
+      th.emplace_back([&, s] {
+        const uint64_t a = n * s / T, b = n * (s + 1) / T;
+        for (auto& v : idx[s]) v.clear();
+        for (uint64_t i = a; i < b; ++i) idx[s][owner(keys[i])].push_back(static_cast<uint32_t>(i));
+      });
+    for (auto& t : th) t.join();
+    th.clear();
+    for (int h = 0; h < T; ++h)
+      th.emplace_back([&, h] {
+        for (int s = 0; s < T; ++s)
+          for (uint32_t i : idx[s][h]) apply(&shard[h], i);
+      });
+    for (auto& t : th) t.join();
+  };
+  const auto t0 = std::chrono::steady_clock::now();
+  phase(ik, n_ins, [&](Dict* d, uint32_t i) { orc_insert(d, ik + i, iv + i, 1, ist ? ist + i : nullptr); });
+  phase(fk, n_find, [&](Dict* d, uint32_t i) {
+    orc_find(d, fk + i, 1, fv ? fv + i : nullptr, ff ? ff + i : nullptr);
+  });
+  phase(mk, n_mix, [&](Dict* d, uint32_t i) {
+    orc_execute(d, mo + i, mk + i, mv + i, 1, mvo ? mvo + i : nullptr, mst ? mst + i : nullptr);
+  });
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
 }  // extern "C"

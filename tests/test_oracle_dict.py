@@ -2,13 +2,16 @@
 
 The dictionary is checked against a brute-force linear-scan list map on tiny
 random op sequences, against the closed form size = inserted - erased, and for
-the order independence that the batch contract promises.
+the order independence that the batch contract promises.  The parallel CPU
+baseline (the dictionary sharded by key over host threads) is checked against
+the dictionary.
 """
 import numpy as np
 import pytest
 
 import oracle
 from oracle import ERASED, FOUND, INSERTED, NOT_FOUND, REPLACED, RESERVED
+from paper_2510_15095_gb300 import workload as W
 
 
 class BruteMap:
@@ -149,3 +152,27 @@ def test_contract_batches_are_order_independent(seed):
         inv = np.argsort(perm)
         results.append((out[inv].tolist(), st[inv].tolist(), [a.tolist() for a in d.dump()]))
     assert results[0] == results[1] == results[2]
+
+
+@pytest.mark.parametrize("threads", [1, 2, 5])
+def test_sharded_baseline_equals_the_dictionary(threads):
+    """The parallel CPU baseline (key-sharded maps on host threads) gives every
+    per-op result the single dictionary gives, whatever the thread count."""
+    rng = np.random.default_rng(70 + threads)
+    keys, c = W.take_keys(71, 0, 20_000)
+    vals = W.values_for(keys, 71)
+    keys[::997] = 0xFFFFFFFF  # reserved keys go through too
+    absent, _ = W.take_keys(71, c, 10_000)
+    fk = np.concatenate([keys[::2], absent])
+    rng.shuffle(fk)
+    d = oracle.Dict()
+    ist = d.insert(keys, vals)
+    fv, ff = d.find(fk)
+    live, _ = d.dump()
+    new, _ = W.take_keys(72, 0, 3_000)
+    ops, mk, mv = W.mixed_batch(rng, live, new, 3_000, 3_000, 6_000, seed=72)
+    mvo, mst = d.execute(ops, mk, mv)
+    sec, a, b, f, e, g = oracle.sharded_step(threads, keys, vals, fk, ops, mk, mv)
+    assert sec > 0
+    for got, exp in ((a, ist), (b, fv), (f, ff), (e, mvo), (g, mst)):
+        assert np.array_equal(got, exp)
