@@ -403,16 +403,11 @@ __device__ __forceinline__ bool stage_round(const View& v, Stage& sg, unsigned n
 // of the warp-uniform ballots.  A home lane that must update the matched slot
 // (erase, replace) does the single CAS itself: the expected word is
 // (value << 32 | key), both of which it now holds.
-//
-// FUSED (the single-kernel batch): a word may be swapped out of its bucket by
-// a concurrent eviction chain, so a failed update CAS sets `retry` (the op
-// probes again) instead of flagging a contract violation, and an op counts as
-// done only once its CAS has succeeded.
-template <int MODE, int S, bool FUSED = false>
+template <int MODE, int S>
 __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb, uint32_t key,
                                       uint32_t val, uint32_t op, int lane, bool& done,
                                       uint8_t& st, uint32_t& outv, uint32_t& fcnt,
-                                      uint32_t& fslot, LaneCounters& cnt, bool& retry) {
+                                      uint32_t& fslot, LaneCounters& cnt) {
   constexpr bool kIns = (MODE == kModeInsert || MODE == kModeMixed);
   constexpr int L = Geo<S>::L, Q = Geo<S>::Q;
   constexpr unsigned LM = Geo<S>::LM;
@@ -468,7 +463,7 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
     if (my_g == g && ((gneed >> my_j) & 1u)) {
       const unsigned hm = (my_m >> (L * my_q)) & LM;
       if (hm) {
-        if (!FUSED) done = true;
+        done = true;
         const uint32_t opk = MODE == kModeMixed
                                  ? op
                                  : (MODE == kModeFind ? OP_FIND
@@ -490,9 +485,6 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
               atomicOr(v.masks + myb, 1u << slot);
               cnt.size_delta -= 1;
               st = ST_ERASED;
-              done = true;
-            } else if (FUSED) {
-              retry = true;
             } else {
               st = ST_ERASED;
               cnt.contract = true;
@@ -502,9 +494,6 @@ __device__ __forceinline__ void probe(const View& v, unsigned need, uint32_t myb
             if (atomicCAS(ull(sp), cur, pack(key, val)) == cur) {
               cnt.replaced += 1;
               st = ST_REPLACED;
-              done = true;
-            } else if (FUSED) {
-              retry = true;
             } else {
               st = ST_REPLACED;
               cnt.contract = true;
@@ -713,8 +702,7 @@ __device__ __forceinline__ void probe_round(const View& v, unsigned need, uint32
       return;
     }
   }
-  bool unused = false;
-  probe<MODE, S>(v, need, myb, key, val, op, lane, done, st, outv, fcnt, fslot, cnt, unused);
+  probe<MODE, S>(v, need, myb, key, val, op, lane, done, st, outv, fcnt, fslot, cnt);
 }
 
 // The paired insert round on staged buckets, one op per lane.  With both
