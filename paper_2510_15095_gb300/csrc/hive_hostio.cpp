@@ -12,6 +12,7 @@
 #include <cstring>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 
 #include "hive.h"
@@ -121,7 +122,7 @@ hive_status run_chunks(hive_table* t, Kind kind, const uint8_t* h_ops, const uin
 // forces it.
 // 0 yes, 1 no, or a CUDA error code from the query.
 cudaError_t query_coherent(int* yes) {
-  static int cached[64] = {};  // 0 unknown, 1 yes, 2 no
+  static std::atomic<int> cached[64];  // 0 unknown, 1 yes, 2 no (zero-initialised)
   *yes = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -130,16 +131,18 @@ cudaError_t query_coherent(int* yes) {
     return e;
   }
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (!cached[dev]) {
+  int c = cached[dev].load(std::memory_order_relaxed);
+  if (!c) {
     int v = 0;
     e = cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return e;
     }
-    cached[dev] = v ? 1 : 2;
+    c = v ? 1 : 2;
+    cached[dev].store(c, std::memory_order_relaxed);
   }
-  *yes = cached[dev] == 1;
+  *yes = c == 1;
   return cudaSuccess;
 }
 
