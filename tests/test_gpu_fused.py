@@ -96,15 +96,16 @@ def test_fused_eviction_beside_lookups(H, slots, bs, load_pct):
     t.close()
 
 
-def test_fused_equals_phased_large(H):
+@pytest.mark.parametrize("bs", [16, 32])
+def test_fused_equals_phased_large(H, bs):
     """2^22 slots at 95% load, 2^20-op batches: the fused and the phased
     launches give identical per-op results and identical maps."""
     slots = 1 << 22
     rng = np.random.default_rng(7)
     keys0, c = W.take_keys(7, 0, slots * 95 // 100)
     vals0 = W.values_for(keys0, 7)
-    a = H.HiveTable(slots, bucket_slots=16)
-    b = H.HiveTable(slots, bucket_slots=16)
+    a = H.HiveTable(slots, bucket_slots=bs)
+    b = H.HiveTable(slots, bucket_slots=bs)
     for t in (a, b):
         t.insert(up(H, keys0), up(H, vals0))
     live = keys0
@@ -170,4 +171,33 @@ def test_fused_ragged_and_reserved(H):
     vo, st = t.execute(torch.zeros(0, dtype=torch.uint8, device="cuda"),
                        torch.zeros(0, dtype=torch.int32, device="cuda"), fused=True)
     assert st.numel() == 0
+    t.close()
+
+
+@pytest.mark.parametrize("bs", [16, 32])
+def test_fused_full_table_reports_full(H, bs):
+    """A mixed batch with more new keys than slots + stash, in one kernel: the
+    inserts that find no room at all report FULL and are not applied; every
+    other op is, finds and erases of the preloaded keys included.  The FULL
+    set is not unique, so the check is that the outcome is valid."""
+    slots = 1 << 10
+    keys0, c = W.take_keys(9, 0, slots // 2)
+    vals0 = W.values_for(keys0, 9)
+    t = H.HiveTable(slots, bucket_slots=bs, stash_permille=0)  # stash floor of 1024 words
+    t.insert(up(H, keys0), up(H, vals0))
+    d = oracle.Dict()
+    d.insert(keys0, vals0)
+    rng = np.random.default_rng(9)
+    new, _ = W.take_keys(9, c, 3000)
+    ops, keys, vals = W.mixed_batch(rng, keys0, new, 3000, 100, 200, seed=9)
+    vo, st = t.execute(torch.from_numpy(ops).cuda(), up(H, keys), up(H, vals), fused=True)
+    st = st.cpu().numpy()
+    full = st == H.FULL
+    assert full.any() and not (full & (ops != 0)).any()  # only inserts can be FULL
+    assert full.sum() >= 3000 + slots // 2 - 100 - (slots + 1024)
+    ev, est = d.execute(ops[~full], keys[~full], vals[~full])
+    assert np.array_equal(st[~full], est)
+    assert np.array_equal(H.to_host_u32(vo)[~full], ev)
+    check_image(t, d)
+    assert t.check() == 4  # HIVE_ERR_FULL
     t.close()
