@@ -516,7 +516,7 @@ hive_status hive_check_batch(const uint8_t* h_ops, uint32_t op, const uint32_t* 
 
 /* ---- Fault injection for tests (host side; the paper has none) ----
  * The library's failure paths -- a bounded wait that gives up, a device
- * allocation that fails -- are made to run by these two calls from the host.
+ * allocation that fails -- are made to run by these calls from the host.
  * Neither makes the GPU fault or hang.
  *
  * hive_debug_fail_alloc: the n-th device allocation the library makes from
@@ -534,9 +534,17 @@ hive_status hive_check_batch(const uint8_t* h_ops, uint32_t op, const uint32_t* 
  * and hive_stats counts lock_timeouts.  Every result stays what the dictionary
  * semantics give.  Free every held lock before the table is used without this
  * hook again.  Returns INVALID_ARG for a bucket not in use, CUDA on a failed
- * memset. */
+ * memset.
+ *
+ * hive_debug_set_versions: sets the bucket version word of every bucket (the
+ * single-kernel batch's eviction-safe lookups) to `value`, stream-ordered on
+ * `stream`: bits 16..31 are the count of finished moves, which a test sets
+ * next to its wrap; bits 0..15, the words in transit, must be 0 (a
+ * quiescent table).  Results are unaffected.  Returns INVALID_ARG for a
+ * non-zero transit count, CUDA on a failed launch. */
 hive_status hive_debug_fail_alloc(uint32_t n);
 hive_status hive_debug_hold_lock(hive_table* t, uint64_t bucket, int held, void* stream);
+hive_status hive_debug_set_versions(hive_table* t, uint32_t value, void* stream);
 
 /* Text of the calling thread's last error (never NULL). */
 const char* hive_last_error(void);

@@ -868,6 +868,16 @@ hive_status hive_debug_hold_lock(hive_table* t, uint64_t bucket, int held, void*
   return HIVE_OK;
 }
 
+hive_status hive_debug_set_versions(hive_table* t, uint32_t value, void* stream) {
+  hive_status st = check_table(t);
+  if (st != HIVE_OK) return st;
+  if (value & 0xFFFFu)
+    return fail(HIVE_ERR_INVALID_ARG, "the low 16 bits (words in transit) must be 0");
+  HIVE_CK(launch_fill_u32(t->locks + t->nb_max, t->nb_max, value,
+                          static_cast<cudaStream_t>(stream)));
+  return HIVE_OK;
+}
+
 hive_status hive_stats(hive_table* t, hive_stats_t* out, void* stream) {
   hive_status st = check_table(t);
   if (st != HIVE_OK) return st;

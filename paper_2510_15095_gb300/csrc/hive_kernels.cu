@@ -1600,28 +1600,31 @@ __global__ void __launch_bounds__(kOvfThreads, HIVE_OVF_MIN_BLOCKS)
 // Here finds, erases, replaces, claims and eviction chains of one batch run
 // at the same time, so a lookup can race with a chain that has taken a word
 // out of a bucket and not yet put it down.  Each bucket has a version word:
-// bits 16..31 count the chains holding, in transit, a word whose BitHash1
-// bucket this is, bits 0..15 count chain steps that finished.  A chain
-// raises the transit count of the BitHash1 bucket of the word it is about to
-// swap out (whichever of its two buckets that word sits in) and lowers it
-// (bumping the step count) once that word sits in its other bucket or in the
-// stash, with a fence on each side.  A lookup of key k reads the version of
+// bits 0..15 count the chains holding, in transit, a word whose BitHash1
+// bucket this is, bits 16..31 count chain steps that finished (modulo 2^16:
+// the count lives as long as the table, and its carry leaves the word
+// instead of reaching the transit count).  A chain raises the transit count
+// of the BitHash1 bucket of the word it is about to swap out (whichever of
+// its two buckets that word sits in) and lowers it (bumping the step count)
+// once that word sits in its other bucket or in the stash, with a fence on
+// each side.  A lookup of key k reads the version of
 // k's BitHash1 bucket before probing and again after a miss: one word covers
 // every move of k.  The miss stands only if no word was in transit there and
 // the version did not move; otherwise the op probes again.  A hit needs no
 // check: the word was observed in place.  Because erases now run beside
 // chains, a chain swaps its victim with a CAS on the word it read (never
 // onto an EMPTY slot); claims then own their slot by its free bit alone.
-constexpr uint32_t kTransit = 1u << 16;
+constexpr uint32_t kTransitMask = 0xFFFFu;  // words in transit
+constexpr uint32_t kStep = 1u << 16;         // one finished step
 constexpr uint32_t kFusedRetryLimit = 1u << 14;
 
 __device__ __forceinline__ void transit_begin(const View& v, uint32_t b) {
-  atomicAdd(v.vers + b, kTransit);
+  atomicAdd(v.vers + b, 1u);
   fence_acq_rel_gpu();
 }
 __device__ __forceinline__ void transit_end(const View& v, uint32_t b) {
   fence_acq_rel_gpu();
-  atomicAdd(v.vers + b, 1u - kTransit);
+  atomicAdd(v.vers + b, kStep - 1u);  // one word fewer in transit, one step more
 }
 
 // Steps 3-4 for one new key whose candidate buckets had no free slot, inside
@@ -2044,7 +2047,7 @@ __device__ void fused_checked(const View& v, uint32_t stash_n, const OpPtrs& a, 
     if (active && !done && !retry) {
       fence_acq_rel_gpu();
       const uint32_t w1 = ld_relaxed32(v.vers + b1);
-      absent = v1 < kTransit && v1 == w1;
+      absent = (v1 & kTransitMask) == 0 && v1 == w1;
     }
   }
 

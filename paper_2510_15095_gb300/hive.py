@@ -37,7 +37,7 @@ EXPORTS = ["hive_config_default", "hive_create", "hive_destroy", "hive_insert", 
            "hive32_find", "hive32_erase", "hive32_execute", "hive32_size", "hive32_clear",
            "hive32_check",
            "hive32_stats", "hive32_dump", "hive_debug_fail_alloc", "hive_debug_hold_lock", "hive_hash",
-           "hive_host_direct_access"]
+           "hive_host_direct_access", "hive_debug_set_versions"]
 KERNEL_KINDS = ["find", "insert", "erase", "mixed", "evict", "maint", "split", "merge", "count",
                 "fused", "claim"]
 
@@ -158,6 +158,7 @@ def load_library(path: str = LIB_PATH):
         L.hive_hash.argtypes = [vp, u64, vp, vp, vp]
         L.hive_debug_hold_lock.argtypes = [vp, u64, i32, vp]
         L.hive_host_direct_access.argtypes = [vp]
+        L.hive_debug_set_versions.argtypes = [vp, C.c_uint32, vp]
         L.hive_last_error.argtypes = []
         L.hive_last_error.restype = C.c_char_p
         for name in EXPORTS:
@@ -421,6 +422,13 @@ class HiveTable:
         b = 0xFFFFFFFFFFFFFFFF if bucket is None else int(bucket)
         _raise(self._L, self._L.hive_debug_hold_lock(self._h, b, 1 if held else 0,
                                                      _stream_ptr(stream)))
+
+    def debug_set_versions(self, value: int, stream=None):
+        """hive_debug_set_versions: set every bucket version word (bits 16..31,
+        the count of finished moves), so that a test can start the
+        single-kernel batch next to the count's wrap."""
+        _raise(self._L, self._L.hive_debug_set_versions(self._h, int(value) & 0xFFFFFFFF,
+                                                        _stream_ptr(stream)))
 
     def dump(self, stream=None) -> dict:
         """Host image of the table (numpy arrays) for checks and checkpoints."""

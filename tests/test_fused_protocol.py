@@ -14,7 +14,11 @@ on the bucket K leaves while the lookup reads only bucket 0's version, the
 same enumeration finds such interleavings, so the check is not vacuous."""
 import itertools
 
-T = 1 << 16  # transit unit of a version word
+# A version word: bits 0..15 count words in transit, bits 16..31 count
+# finished moves (modulo 2^16: the carry leaves the 32-bit word).
+MOVE = 1 << 16
+TRANSIT = MOVE - 1
+WORD = (1 << 32) - 1
 
 
 STASH = 2  # the stash, as a third place K can be
@@ -39,10 +43,10 @@ def chain_steps(moves, marks="key"):
 READER = [("v0",), ("probe", 0), ("probe", 1), ("probe", STASH), ("v1",)]
 
 
-def run(order, writer, start):
+def run(order, writer, start, ver0=0):
     """Execute one interleaving; returns the lookup's verdict."""
     where = {start}
-    ver = [0, 0, 0]
+    ver = [ver0, 0, 0]
     wi = ri = 0
     found = False
     v_before = v_after = None
@@ -51,9 +55,9 @@ def run(order, writer, start):
             op, b = writer[wi]
             wi += 1
             if op == "mark":
-                ver[b] += T
+                ver[b] = (ver[b] + 1) & WORD
             elif op == "unmark":
-                ver[b] += 1 - T
+                ver[b] = (ver[b] + MOVE - 1) & WORD
             elif op == "out":
                 where.discard(b)
             else:
@@ -69,18 +73,18 @@ def run(order, writer, start):
                 v_after = ver[0]
     if found:
         return "hit"
-    quiet = v_before < T and v_before == v_after
+    quiet = (v_before & TRANSIT) == 0 and v_before == v_after
     return "miss" if quiet else "retry"
 
 
-def verdicts(writer, start):
+def verdicts(writer, start, ver0=0):
     n_w, n_r = len(writer), len(READER)
     out = set()
     for pos in itertools.combinations(range(n_w + n_r), n_r):
         order = ["w"] * (n_w + n_r)
         for p in pos:
             order[p] = "r"
-        out.add(run(order, writer, start))
+        out.add(run(order, writer, start, ver0))
     return out
 
 
@@ -129,3 +133,23 @@ def test_marks_on_the_left_bucket_miss_with_one_version_read():
 
 def test_a_quiet_table_gives_hits():
     assert verdicts([], start=0) == {"hit"}
+
+
+def test_the_move_counter_wraps_without_touching_the_transit_count():
+    # a version whose move counter is about to wrap: a move during the
+    # lookup is still caught, and once the move is over a lookup of an absent
+    # key settles (a carry into the transit count would make every later
+    # lookup retry for ever)
+    near = (MOVE - 1) * MOVE
+    assert "miss" not in verdicts(chain_steps([(0, 1), (1, 0)]), start=0, ver0=near)
+    # another key's move, sharing version word 0, finishes before a lookup of
+    # an absent key (kept at a place no lookup probes)
+    other = [("mark", 0), ("unmark", 0)]
+    done_first = run(["w"] * len(other) + ["r"] * len(READER), other, start=99, ver0=near)
+    assert done_first == "miss"
+    # after 2^16 finished moves on one word the transit count is still 0
+    v = 0
+    for _ in range(MOVE + 3):
+        v = (v + 1) & WORD
+        v = (v + MOVE - 1) & WORD
+    assert v & TRANSIT == 0

@@ -201,3 +201,33 @@ def test_fused_full_table_reports_full(H, bs):
     check_image(t, d)
     assert t.check() == 4  # HIVE_ERR_FULL
     t.close()
+
+
+@pytest.mark.parametrize("bs", [16, 32])
+def test_fused_version_count_wraps(H, bs):
+    """Every bucket's count of finished moves starts one short of its wrap:
+    chains beside Zipf-skewed finds and erases wrap it, and lookups still
+    settle (no TIMEOUT) with every result the oracle's."""
+    slots = 1 << 12
+    seed = 40 + bs
+    rng = np.random.default_rng(seed)
+    t = H.HiveTable(slots, bucket_slots=bs, stash_permille=50)
+    with pytest.raises(H.HiveError):
+        t.debug_set_versions(1)  # words in transit: refused
+    t.debug_set_versions(0xFFFF << 16)
+    d = oracle.Dict()
+    live, c = W.take_keys(seed, 0, slots * 95 // 100)
+    t.insert(up(H, live), up(H, W.values_for(live, seed)))
+    d.insert(live, W.values_for(live, seed))
+    over = 0
+    for b in range(6):
+        new, c = W.take_keys(seed, c, 128)
+        ops, keys, vals = W.mixed_batch(rng, live, new, 128, 128, 512, seed=seed + b, zipf_s=0.99)
+        before = t.stats()["overflowed"]
+        run_batch(H, t, d, ops, keys, vals, f"batch {b}")
+        over += t.stats()["overflowed"] - before
+        live, _ = d.dump()
+        check_image(t, d)
+    assert over > 0, "no insert reached the eviction chain"
+    assert t.check() == 0  # no lookup ran out of retries
+    t.close()
