@@ -227,8 +227,9 @@ hive_status hive_execute(hive_table* t, const uint8_t* ops, const uint32_t* keys
  * launch).  Finds, erases, replaces, claims, cuckoo eviction chains
  * (Algorithm 3) and stash appends of the batch all run at once.  A lookup
  * that misses while a chain is moving a word out of one of its candidate
- * buckets is repeated: each bucket carries a version word that chains raise
- * and lower around the move, and a miss counts only if both versions were
+ * buckets is repeated: each bucket carries a version word that a chain
+ * raises and lowers around the move of any word whose BitHash1 bucket it
+ * is, and a miss counts only if the version of the key's BitHash1 bucket was
  * quiet and unchanged across the probe.  Arguments, per-op results, the batch
  * contract and the errors are exactly those of hive_execute(), and so are
  * the results.  A resizable table grows before the kernel as in
