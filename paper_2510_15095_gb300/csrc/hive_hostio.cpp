@@ -120,7 +120,9 @@ hive_status run_chunks(hive_table* t, Kind kind, const uint8_t* h_ops, const uin
 // 1.83, insert 4.08 against 4.60.  Pageable arrays, and every array on other
 // GPUs, take the staged path; HIVE_HOSTIO_STAGED=1 in the environment
 // forces it.
-// 0 yes, 1 no, or a CUDA error code from the query.
+//
+// query_coherent: *yes = whether the current device has that access (cached
+// per device); returns the CUDA error of the query, if any.
 cudaError_t query_coherent(int* yes) {
   static std::atomic<int> cached[64];  // 0 unknown, 1 yes, 2 no (zero-initialised)
   *yes = 0;
